@@ -1,0 +1,421 @@
+#!/usr/bin/env python
+"""Benchmark of the sliCQ hot path: forward + inverse of a 60 s stereo clip.
+
+One step = slicq_forward (Algorithm 3: slicing, real FFT_2N, band multiply
+and fold, per-band inverse FFT) + slicq_inverse (Algorithm 4: per-band FFT,
+dual-window multiply and overlap into the slice spectrum, inverse real
+FFT_2N, overlap-add) of 2 x 2,646,000 samples at 44.1 kHz with B = 48,
+fmin = 32.7 Hz, fmax = 22050 Hz, 2N = 65536, M = 16384 (Hann windows).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
+
+Prints one JSON line (rank 0).  The L2 cache is flushed (256 MiB write)
+between timed steps, outside the per-step CUDA events.  N > 1 runs N
+independent replicas (one clip per GPU; the transform has no exchange step).
+--impl reference times the FP64 CPU oracle (the only other implementation
+of the method) on the host cores instead.
+"""
+
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "sliCQ fwd+inv audio samples/s on 1 GB300 at rel. err ≤1e-5; % HBM roofline"
+UNIT = "samples/s"
+WORKLOAD = dict(fs=44100.0, fmin=32.7, fmax=22050.0, bins_per_octave=48, slice_len=65536,
+                trans_len=16384, seconds=60, channels=2)
+WORKLOAD_NAME = ("60 s stereo 44.1 kHz, pink noise + 20 decaying harmonic tones; Hann CQ windows "
+                 "B=48, fmin=32.7 Hz, fmax=22050 Hz; slice 2N=65536, transition 16384")
+KERNELS = ("slice_forward", "band_analysis", "band_synthesis", "slice_inverse")
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def _source_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_1210_0084_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def _ncu_traffic(kernel):
+    """DRAM bytes per launch of `kernel` from the committed ncu summary, if it
+    was taken on the current kernel sources; else None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.txt")
+    if not os.path.exists(path):
+        return None
+    sha = _source_sha()
+    for line in open(path):
+        kv = dict(tok.split("=", 1) for tok in line.split() if "=" in tok)
+        if kv.get("kernel") == kernel and kv.get("source_sha") == sha:
+            try:
+                return float(kv["dram_bytes_per_launch"])
+            except (KeyError, ValueError):
+                return None
+    return None
+
+
+# --------------------------------------------------------------- clocks ---
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the GPU works."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id: str):
+        self.proc = None
+        self.samples = []
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", gpu_id, f"--query-gpu=timestamp,{self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "20"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        for line in out.splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                self.samples.append(dict(sm=float(parts[1]), sm_max=float(parts[2]),
+                                         hw=parts[5], hw_th=parts[6], sw_th=parts[7],
+                                         sw_pc=parts[8]))
+            except ValueError:
+                pass
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [s["sm"] for s in self.samples]
+        reasons = set()
+        for s in self.samples:
+            for key, name in (("hw", "hw_slowdown"), ("hw_th", "hw_thermal_slowdown"),
+                              ("sw_th", "sw_thermal_slowdown"), ("sw_pc", "sw_power_cap")):
+                if s[key].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(s["sm_max"] for s in self.samples),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------- CPU oracle ---
+
+def _oracle_job(args):
+    """FP64 oracle forward + inverse of one segment (runs in a spawned worker)."""
+    seg, p = args
+    import numpy as np
+    import oracle as O
+    plan = O.make_plan(O.SliCQParams(*p))
+    c = O.slicq_forward(seg.astype(np.float64), plan)
+    y = O.slicq_inverse(c, plan, seg.shape[0])
+    return seg.shape[0], float(np.linalg.norm(y - seg) / np.linalg.norm(seg))
+
+
+def _oracle_pool(workers):
+    import multiprocessing as mp
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    return mp.get_context("spawn").Pool(workers)
+
+
+def _oracle_segments(x, count, seg_len):
+    n = x.shape[-1]
+    segs = []
+    for i in range(count):
+        ch = i % x.shape[0]
+        off = (i * 7919 * seg_len) % max(1, n - seg_len)
+        segs.append(x[ch, off:off + seg_len].copy())
+    return segs
+
+
+def _oracle_params():
+    w = WORKLOAD
+    return (w["fs"], w["fmin"], w["fmax"], w["bins_per_octave"], w["slice_len"], w["trans_len"])
+
+
+def cpu_baseline(x, seconds_target=15.0):
+    """Time the oracle on the host cores over a bounded sample of the workload."""
+    cores = os.cpu_count() or 1
+    seg_len = 2 * WORKLOAD["slice_len"]      # 4 slices of the workload's plan per job
+    pool = _oracle_pool(cores)
+    try:
+        pool.map(_oracle_job, [(s, _oracle_params()) for s in _oracle_segments(x, cores, WORKLOAD["slice_len"])])
+        jobs, done, t0 = 0, 0, time.perf_counter()
+        while time.perf_counter() - t0 < seconds_target and jobs < 64 * cores:
+            segs = _oracle_segments(x[:, (jobs * 131) % 1000:], cores, seg_len)
+            res = pool.map(_oracle_job, [(s, _oracle_params()) for s in segs])
+            done += sum(r[0] for r in res)
+            jobs += cores
+        dt = time.perf_counter() - t0
+    finally:
+        pool.close()
+        pool.join()
+    return {"value": done / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"{jobs} segments of {seg_len} samples of the workload (FP64 forward + "
+                      f"inverse per segment, one process per core, {dt:.1f} s wall)"}
+
+
+def run_reference(args, x, rank, world):
+    if rank != 0:
+        return
+    cores = os.cpu_count() or 1
+    seg_len = WORKLOAD["slice_len"]
+    pool = _oracle_pool(cores)
+    times, samples = [], 0
+    try:
+        for i in range(args.warmup + args.steps):
+            segs = _oracle_segments(x[:, (i * 97) % 1000:], cores, seg_len)
+            t0 = time.perf_counter()
+            res = pool.map(_oracle_job, [(s, _oracle_params()) for s in segs])
+            dt = time.perf_counter() - t0
+            if i >= args.warmup:
+                times.append(dt)
+                samples = sum(r[0] for r in res)
+    finally:
+        pool.close()
+        pool.join()
+    ms = 1e3 * statistics.mean(times)
+    value = samples / (ms / 1e3)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": _config(world),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"each step: {cores} segments of {seg_len} samples of the "
+                                   "workload, FP64 forward + inverse, one process per core"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def _config(world):
+    return {"workload": WORKLOAD_NAME, "fs": WORKLOAD["fs"], "bins_per_octave": WORKLOAD["bins_per_octave"],
+            "fmin": WORKLOAD["fmin"], "fmax": WORKLOAD["fmax"], "slice_len": WORKLOAD["slice_len"],
+            "trans_len": WORKLOAD["trans_len"], "channels": WORKLOAD["channels"],
+            "samples_per_channel": WORKLOAD["seconds"] * int(WORKLOAD["fs"]),
+            "mk_policy": "pow2", "l2": "flushed between timed steps (256 MiB write, outside the events)",
+            "parallelism": f"replicas x{world} (independent clips, no exchange)"}
+
+
+# ---------------------------------------------------------------- native ---
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=("native", "reference"), default="native")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=10)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local_rank = _env_int("LOCAL_RANK", 0)
+
+    import numpy as np
+    from paper_1210_0084_gb300 import signals
+
+    n = WORKLOAD["seconds"] * int(WORKLOAD["fs"])
+    x = signals.pink_noise_harmonic_tones(n, WORKLOAD["fs"], WORKLOAD["channels"],
+                                          seed=signals.seed_for(1, rank))
+    if args.impl == "reference":
+        run_reference(args, x, rank, world)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    if local_rank == 0:
+        from paper_1210_0084_gb300 import build as B
+        B.build()
+    if world > 1:
+        dist.barrier()
+    from paper_1210_0084_gb300.slicq import SliCQParams, SliCQPlan
+
+    p = SliCQParams(WORKLOAD["fs"], WORKLOAD["fmin"], WORKLOAD["fmax"], WORKLOAD["bins_per_octave"],
+                    WORKLOAD["slice_len"], WORKLOAD["trans_len"])
+    plan = SliCQPlan(p, local_rank)
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    batch = x.shape[0]
+    xd = torch.from_numpy(x).to(dev)
+    S = plan.num_slices(n)
+    c = torch.empty((batch, S, plan.coefs_per_slice), dtype=torch.complex64, device=dev)
+    y = torch.empty((batch, n), dtype=torch.float32, device=dev)
+    plan.workspace(n, batch)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        plan.forward(xd, out=c)
+        plan.inverse(c, n, out=y)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    recon_err = float(torch.linalg.norm(y - xd) / torch.linalg.norm(xd))
+
+    props = torch.cuda.get_device_properties(dev)
+    gpu_id = getattr(props, "pci_bus_id", None) or str(local_rank)
+    # keep the GPU busy for ~1 s before the timed region so the clock samples
+    # below see the loaded state
+    sampler = ClockSampler(str(gpu_id))
+    t_end = time.perf_counter() + 1.0
+    while time.perf_counter() < t_end:
+        for _ in range(20):
+            step()
+        torch.cuda.synchronize()
+
+    plan.trace(True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.fill_(i & 255)
+        starts[i].record(stream)
+        step()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    # a second second of load, so that short timed regions still get samples
+    t_end = time.perf_counter() + 0.5
+    while time.perf_counter() < t_end:
+        for _ in range(20):
+            step()
+        torch.cuda.synchronize()
+    sampler.stop()
+    traced = plan.trace_read()
+    plan.trace(False)
+
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = statistics.mean(step_ms)
+    ms_t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = float(ms_t.item())
+    samples_all = batch * n * world
+    value = samples_all / (ms_max / 1e3)
+
+    # per-kernel launch times (events around each launch on the call's stream)
+    per = {k: [] for k in KERNELS}
+    for name, t in traced:
+        per[name].append(t)
+    cps = plan.coefs_per_slice
+    alg_bytes = {"slice_forward": batch * n * 4, "band_analysis": batch * S * cps * 8,
+                 "band_synthesis": batch * S * cps * 8, "slice_inverse": batch * n * 4}
+    peak, peak_kind = _peaks()
+    kern = {}
+    for k in KERNELS:
+        if per[k]:
+            avg = statistics.mean(per[k])
+            kern[k] = {"launches": len(per[k]), "avg_ms": avg, "share": sum(per[k]),
+                       "alg_bytes_per_launch": alg_bytes[k],
+                       "gbs": alg_bytes[k] / (avg * 1e-3) / 1e9}
+    tot = sum(v["share"] for v in kern.values()) or 1.0
+    for v in kern.values():
+        v["share"] = v["share"] / tot
+    dom = max(kern, key=lambda k: kern[k]["share"])
+    traffic = _ncu_traffic(dom)
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": kern[dom]["gbs"], "peak": peak,
+                "unit": "GB/s", "frac": kern[dom]["gbs"] / peak, "traffic": traffic,
+                "peak_kind": f"of {peak_kind}"}
+    step_bytes = batch * (8 * n + 16 * S * cps)
+    step_roof = {"alg_bytes": step_bytes, "achieved": step_bytes / (ms * 1e-3) / 1e9,
+                 "frac": step_bytes / (ms * 1e-3) / 1e9 / peak}
+
+    # end to end through the public API with pinned host buffers
+    xh = torch.from_numpy(x).pin_memory()
+    yh = torch.empty((batch, n), dtype=torch.float32).pin_memory()
+    xin = torch.empty_like(xd)
+    e_ms = []
+    for i in range(args.warmup + args.e2e_steps):
+        flush.fill_(i & 255)
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        xin.copy_(xh, non_blocking=True)
+        plan.forward(xin, out=c)
+        plan.inverse(c, n, out=y)
+        yh.copy_(y, non_blocking=True)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        if i >= args.warmup:
+            e_ms.append(s0.elapsed_time(s1))
+    e2e_err = float(np.linalg.norm(yh.numpy() - x) / np.linalg.norm(x))
+    e_ms_t = torch.tensor([statistics.mean(e_ms)], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(e_ms_t, op=dist.ReduceOp.MAX)
+    e2e = {"value": samples_all / (float(e_ms_t.item()) / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": int(xh.numel() * 4), "d2h_bytes_per_step": int(yh.numel() * 4),
+           "ms_per_step": float(e_ms_t.item()), "recon_rel_err": e2e_err}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cpu = cpu_baseline(x)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": _config(world), "recon_rel_err": recon_err,
+            "roofline": roofline, "step_roofline": step_roof, "kernels": kern,
+            "gpu_launches": len(traced), "e2e": e2e, "cpu_baseline": cpu,
+            "clocks": sampler.summary(), "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms),
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,217 @@
+/*
+ * slicq.h — C ABI of the GB300 sliCQ library (libslicq.so).
+ *
+ * The sliced constant-Q nonstationary Gabor transform (sliCQ) of Holighaus,
+ * Doerfler, Velasco and Grill, "A framework for invertible, real-time
+ * constant-Q transforms" (arXiv:1210.0084):
+ *   forward  = Algorithm 3 (sliCQ analysis), each slice by Algorithm 1,
+ *   inverse  = Algorithm 4 (sliCQ synthesis), each slice by Algorithm 2 with
+ *              the canonical dual of Proposition 2 (eq. painlessframe2),
+ *   adjoint  = the adjoint of the forward map (frame synthesis with the
+ *              analysis windows, Sec. 2.1 eq. frameop), used as its gradient.
+ *
+ * Conventions shared by every entry point
+ *   - Signals are real float32, channel-major: d_f[b * n_samples + t],
+ *     b < batch, t < n_samples.
+ *   - Coefficients are complex float32 stored as interleaved (re, im) pairs,
+ *     slice-major: coefficient n of channel k of slice m of signal b is the
+ *     pair at index ((b * S + m) * C_s + off_k + n), with S =
+ *     slicq_num_slices(), C_s = coefs_per_slice, off_k = sum_{i<k} M_i,
+ *     n < M_k, k = 0..K+1 (the channels that a real signal needs, Table 1;
+ *     channels K+2..2K+1 are the complex conjugates of K..1).  The paper's
+ *     2-layer array s^l (Sec. 4.1) is the index map l = m mod 2,
+ *     n_layer = (n + (m-1) M_k / 2) mod (S M_k / 2).
+ *   - Coefficients are the frame coefficients c_{n,k} = <f^m, phi_{n,k}>
+ *     with the unitary DFT of Sec. 2.1 (eq. CQ_coeff).
+ *   - All pointers named d_* are device pointers on the plan's device and are
+ *     owned by the caller.  Host pointers are named h_*.
+ *   - Calls that take a stream are asynchronous on that stream.  They return
+ *     argument errors before launching anything and launch errors at once;
+ *     faults inside a kernel surface at the next synchronising call.
+ *   - No entry point allocates device memory except slicq_plan_create.
+ *   - Nothing throws across the ABI; every call returns a slicq_status.
+ */
+#ifndef SLICQ_H
+#define SLICQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+#include <cuda_runtime_api.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SLICQ_ABI_VERSION 1
+
+#if defined(__GNUC__)
+#define SLICQ_API __attribute__((visibility("default")))
+#else
+#define SLICQ_API
+#endif
+
+typedef enum {
+  SLICQ_OK = 0,
+  SLICQ_EINVAL = 1,       /* invalid parameter or null pointer */
+  SLICQ_ENOMEM = 2,       /* device or host allocation failed (plan only) */
+  SLICQ_ECUDA = 3,        /* a CUDA runtime call or launch failed */
+  SLICQ_ESIZE = 4,        /* a caller buffer is too small */
+  SLICQ_ETIMEOUT = 5,     /* a bounded device wait gave up */
+  SLICQ_EUNSUPPORTED = 6  /* valid parameters outside what this build runs */
+} slicq_status;
+
+typedef enum { SLICQ_WIN_HANN = 0 } slicq_window;          /* H of Sec. 3 */
+typedef enum { SLICQ_MK_POW2 = 0 } slicq_mk_policy;         /* M_k choice */
+
+/*
+ * Parameters of one sliCQ system (Sec. 3 and Sec. 4).
+ *   fs, fmin, fmax   xi_s, xi_min, xi_max in Hz (Table 1); 0 < fmin < fmax.
+ *                    fmax at or above fs/2 selects the largest K with
+ *                    xi_K < fs/2.
+ *   bins_per_octave  B >= 1.
+ *   slice_len        2N, the FFT length of one slice, a power of two in
+ *                    [2048, 131072].
+ *   trans_len        M, the Tukey transition length, even, 2 <= M < N.
+ *   min_filter_len   lower bound on the support of g_k in samples (Sec. 5.2;
+ *                    16 is the paper's recommendation). >= 1.
+ *   window           SLICQ_WIN_HANN.
+ *   mk_policy        SLICQ_MK_POW2: M_k = max(16, next power of two >= |J_k|).
+ *   slice_cluster    CTAs per slice FFT (thread-block cluster size); 0 picks
+ *                    the default.  Must be a power of two <= 8 if given.
+ */
+typedef struct {
+  double fs;
+  double fmin;
+  double fmax;
+  int32_t bins_per_octave;
+  int32_t min_filter_len;
+  int64_t slice_len;
+  int64_t trans_len;
+  int32_t window;
+  int32_t mk_policy;
+  int32_t slice_cluster;
+  int32_t reserved;
+} slicq_params;
+
+typedef struct slicq_plan slicq_plan;
+
+/* Human-readable name of a status code (static storage, never NULL). */
+SLICQ_API const char* slicq_status_string(slicq_status s);
+
+/* ABI version of the loaded library (SLICQ_ABI_VERSION). */
+SLICQ_API int32_t slicq_abi_version(void);
+
+/*
+ * Host-only layout query (no device needed).  Computes K and the channel
+ * layout of Table 1 with the supports J_k of Sec. 3.
+ *   n_channels       out: K + 2 (the kept channels 0..K+1).
+ *   coefs_per_slice  out: sum_k M_k.
+ * Returns SLICQ_EINVAL for invalid parameters, SLICQ_EUNSUPPORTED for valid
+ * ones this build does not run (e.g. an M_k above 1024).
+ */
+SLICQ_API slicq_status slicq_layout(const slicq_params* p, int32_t* n_channels,
+                          int64_t* coefs_per_slice);
+
+/*
+ * Host-only per-channel tables, each an array of n_channels entries owned by
+ * the caller (any may be NULL):
+ *   h_M       M_k                      h_off    off_k (coefficient offset)
+ *   h_j0      first support sample of g_k on Z_{2N} (0 <= j0 < 2N)
+ *   h_len     |J_k|                    h_xi, h_omega   xi_k, Omega_k in Hz
+ */
+SLICQ_API slicq_status slicq_layout_tables(const slicq_params* p, int32_t n_channels,
+                                 int32_t* h_M, int64_t* h_off, int64_t* h_j0,
+                                 int32_t* h_len, double* h_xi, double* h_omega);
+
+/*
+ * Build a plan on `device`: integer layout on the host, window, dual-window
+ * (reciprocal of sum_k M_k g_k^2, Prop. 2), slicing-window and twiddle
+ * tables in FP64 on the device, stored as float32.  Synchronous.  The plan
+ * owns its device tables; free with slicq_plan_destroy.
+ */
+SLICQ_API slicq_status slicq_plan_create(const slicq_params* p, int device,
+                               slicq_plan** out);
+SLICQ_API void slicq_plan_destroy(slicq_plan* plan);
+
+/* K + 2 and sum_k M_k of a plan. */
+SLICQ_API slicq_status slicq_plan_info(const slicq_plan* plan, int32_t* n_channels,
+                             int64_t* coefs_per_slice);
+
+/* Number of slices L/N for n_samples (L = 2N ceil(n/2N), Sec. 4.1); 0 on error. */
+SLICQ_API int64_t slicq_num_slices(const slicq_plan* plan, int64_t n_samples);
+
+/*
+ * Device workspace (bytes) that forward / inverse / adjoint need for
+ * `batch` signals of n_samples.  The workspace holds slice spectra and the
+ * small hand-off areas that make the overlap-adds deterministic.  It must be
+ * zero-filled once after allocation; every completed call leaves it ready
+ * for the next.  Calls that share a workspace must not overlap in time.
+ */
+SLICQ_API slicq_status slicq_workspace_size(const slicq_plan* plan, int64_t n_samples,
+                                  int64_t batch, size_t* bytes);
+
+/*
+ * Forward sliCQ (Algorithm 3 with Algorithm 1 per slice) of `batch` real
+ * signals.  d_coef receives batch * S * coefs_per_slice complex values;
+ * coef_capacity is its size in complex values (SLICQ_ESIZE if too small).
+ */
+SLICQ_API slicq_status slicq_forward(const slicq_plan* plan, const float* d_f,
+                           int64_t n_samples, int64_t batch, float* d_coef,
+                           int64_t coef_capacity, void* d_work,
+                           size_t work_bytes, cudaStream_t stream);
+
+/*
+ * Inverse sliCQ (Algorithm 4 with Algorithm 2 per slice, canonical dual,
+ * dual slicing window = indicator of the support of h_0), real output of
+ * n_samples per signal.  For coefficients of a real signal this is its
+ * perfect reconstruction (Prop. 3); for other coefficients it is the real
+ * part of the synthesis with the conjugate channels restored.
+ */
+SLICQ_API slicq_status slicq_inverse(const slicq_plan* plan, const float* d_coef,
+                           int64_t n_samples, int64_t batch, float* d_out,
+                           void* d_work, size_t work_bytes,
+                           cudaStream_t stream);
+
+/*
+ * Adjoint of the forward map for real input: d_out = Re(A^H c), i.e. the
+ * synthesis of Algorithm 2 with the analysis windows g_k over channels
+ * 0..K+1 and overlap-add with h_0.  This is the gradient of a real loss with
+ * respect to the signal given the conjugate-Wirtinger gradient d_coef.
+ */
+SLICQ_API slicq_status slicq_adjoint(const slicq_plan* plan, const float* d_coef,
+                           int64_t n_samples, int64_t batch, float* d_out,
+                           void* d_work, size_t work_bytes,
+                           cudaStream_t stream);
+
+/*
+ * Copy a plan table to host memory (tests and diagnostics; synchronous).
+ *   which = 0  analysis windows g_k / sqrt(2N), channels 0..K+1 concatenated
+ *          1  synthesis windows w_k g~_k / sqrt(2N) (w_k = 1/2 for k = 0, K+1)
+ *          2  adjoint windows g_k / (2 sqrt(2N))
+ *          3  Tukey transition h_0 at |j - N| = (N-M)/2 + o, o = 0..M
+ *   count  capacity of h_out in floats; SLICQ_ESIZE if too small.
+ *   n_out  out: number of floats written.
+ */
+SLICQ_API slicq_status slicq_plan_table(const slicq_plan* plan, int32_t which,
+                              float* h_out, int64_t count, int64_t* n_out);
+
+/*
+ * Kernel timing trace (diagnostics and benchmarking; not part of the
+ * paper's method).  With enable != 0 every later forward / inverse /
+ * adjoint call on this plan records a CUDA event on its stream before and
+ * after each kernel launch (up to 4096 launches; later ones are not traced).
+ * Kernel ids: 0 slice forward (slicing + real FFT), 1 band analysis,
+ * 2 band synthesis, 3 slice inverse (real inverse FFT + overlap-add).
+ * slicq_trace_read waits for the recorded events, writes up to `cap`
+ * (kernel id, milliseconds) pairs to host arrays and clears the trace.
+ * enable = 0 releases the events.  Not thread-safe with concurrent calls
+ * on the same plan.
+ */
+SLICQ_API slicq_status slicq_trace_enable(const slicq_plan* plan, int32_t enable);
+SLICQ_API slicq_status slicq_trace_read(const slicq_plan* plan, int32_t* h_kernel,
+                                        float* h_ms, int32_t cap, int32_t* n_out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SLICQ_H */

@@ -1,0 +1,135 @@
+// Internal plan representation and launcher declarations of libslicq.
+// Host and device code of the library include this; it is not installed.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "slicq.h"
+
+namespace slicq {
+
+// Threads of one band-group CTA, and complex values each thread holds.
+constexpr int kBandThreads = 256;
+constexpr int kPerThread = 32;
+constexpr int kMaxBandLog2 = 10;  // M_k <= 1024 (two register passes of <= 32)
+constexpr int kMinBandLog2 = 4;   // M_k >= 16
+constexpr int kSliceMaxThreads = 256;  // slice kernels: N / (32 C) <= 256
+constexpr int64_t kMaxGridY = 65535;
+
+// One kept channel k = 0..K+1 on the slice circle Z_{2N} (Sec. 3).
+struct BandDesc {
+  int32_t j0;        // first support bin, 0 <= j0 < 2N (circular)
+  int32_t len;       // |J_k|
+  int32_t log2M;     // M_k = 1 << log2M
+  int32_t coef_off;  // off_k inside one slice's coefficients
+  int32_t win_off;   // offset into the window tables
+  int32_t tofs;      // first thread of the band's team inside the group CTA
+  int32_t smem_off;  // complex offset of the team's buffer in shared memory
+  int32_t color;     // accumulation colour (disjoint footprints per colour)
+  int32_t mirror;    // 1 if some support bin maps to the half spectrum mirrored
+  int32_t pad_;
+};
+
+// A CTA's worth of consecutive channels for the band kernels.
+struct GroupDesc {
+  int32_t band_begin, band_end;  // channels [begin, end)
+  int32_t acc_lo, acc_hi;        // half-spectrum bins the group touches
+  int32_t ex_lo, ex_hi;          // bins only this group touches
+  int32_t ncolor;                // colour classes
+  int32_t any_mirror;            // some band has mirrored bins
+  int32_t left_bd, right_bd;     // boundary indices, -1 if none
+};
+
+// Bins [lo, hi) touched by two neighbouring groups (bd and bd + 1).
+struct BoundaryDesc {
+  int32_t lo, hi;
+};
+
+// Which of the plan's window tables a synthesis launch uses.
+enum SynthKind { kSynthInverse = 0, kSynthAdjoint = 1 };
+
+}  // namespace slicq
+
+struct slicq_plan {
+  slicq_params params;
+  int device = 0;
+  int K = 0;
+  int n_channels = 0;
+  int64_t N = 0;          // half slice length
+  int64_t coefs_per_slice = 0;
+  int logP = 0, logQ = 0; // four-step split of the N-point complex FFT
+  int C = 1;              // cluster size of the slice kernels
+  int G = 0;              // band groups
+  int max_ovl = 0;        // longest group-boundary overlap (bins)
+  int band_smem = 0;      // dynamic shared memory of the band kernels (bytes)
+  int slice_smem = 0;     // dynamic shared memory of the slice kernels (bytes)
+  int tw_lb = 0;          // log2 of the fine twiddle table length
+  int64_t win_total = 0;  // sum_k |J_k|
+
+  std::vector<slicq::BandDesc> bands;
+  std::vector<slicq::GroupDesc> groups;
+  std::vector<slicq::BoundaryDesc> bounds;
+  std::vector<int16_t> thread_band;  // [G][kBandThreads] channel or -1
+  std::vector<double> xi, omega;     // Table 1, channels 0..K+1
+  std::vector<int64_t> jlo;          // unwrapped first support sample
+
+  // device arena (one allocation)
+  void* d_arena = nullptr;
+  slicq::BandDesc* d_bands = nullptr;
+  slicq::GroupDesc* d_groups = nullptr;
+  slicq::BoundaryDesc* d_bounds = nullptr;
+  int16_t* d_thread_band = nullptr;
+  float* d_ga = nullptr;    // g_k / sqrt(2N)
+  float* d_gs = nullptr;    // w_k g~_k / sqrt(2N)
+  float* d_gadj = nullptr;  // g_k / (2 sqrt(2N))
+  float* d_hw = nullptr;    // Tukey transition, M + 1 values
+  float2* d_tw_lo = nullptr;  // exp(-2 pi i t / 2N), t < 2^tw_lb
+  float2* d_tw_hi = nullptr;  // exp(-2 pi i (t << tw_lb) / 2N)
+
+  // optional kernel timing trace (events around every launch)
+  struct Trace {
+    bool on = false;
+    int n = 0;
+    std::vector<cudaEvent_t> ev;  // 2 per slot
+    std::vector<int32_t> kid;
+  };
+  mutable Trace trace;
+};
+
+namespace slicq {
+
+// Host layout (no device): fills everything in `pl` above the arena.
+slicq_status build_layout(const slicq_params* p, slicq_plan* pl);
+
+// Workspace partition for (n_samples, batch).
+struct Workspace {
+  int64_t S = 0, L = 0;
+  int64_t spec_stride = 0;         // complex values per slice spectrum row
+  float2* spec = nullptr;          // [batch * S][spec_stride]
+  float2* band_patch = nullptr;    // [batch * S][G - 1][2][max_ovl]
+  uint32_t* band_cnt = nullptr;    // [batch * S][G - 1]
+  float* ola_patch = nullptr;      // [batch * S][2][M]
+  uint32_t* ola_cnt = nullptr;     // [batch * S][C]
+  size_t bytes = 0;
+};
+size_t workspace_layout(const slicq_plan* pl, int64_t n_samples, int64_t batch,
+                        void* base, Workspace* ws);
+
+// Kernel launchers (return cudaGetLastError() of the launch).
+cudaError_t launch_slice_forward(const slicq_plan* pl, const float* f,
+                                 int64_t n, int64_t batch, const Workspace& ws,
+                                 cudaStream_t st);
+cudaError_t launch_band_analysis(const slicq_plan* pl, const Workspace& ws,
+                                 int64_t batch, float2* coef, cudaStream_t st);
+cudaError_t launch_band_synthesis(const slicq_plan* pl, const float2* coef,
+                                  int64_t batch, SynthKind kind,
+                                  const Workspace& ws, cudaStream_t st);
+cudaError_t launch_slice_inverse(const slicq_plan* pl, int64_t n,
+                                 int64_t batch, SynthKind kind,
+                                 const Workspace& ws, float* out,
+                                 cudaStream_t st);
+
+}  // namespace slicq

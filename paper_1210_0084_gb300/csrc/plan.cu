@@ -1,0 +1,460 @@
+// Plan construction: the integer layout on the host and the window, dual
+// window and twiddle tables in FP64 on the device (stored as float32).
+//
+//   Table 1 (Sec. 3)       centre frequencies xi_k and bandwidths Omega_k,
+//                          K the smallest integer with xi_K >= xi_max,
+//                          decreased while xi_K >= xi_s / 2.
+//   Sec. 3 sampling        g_k[j] = H((j xi_s / 2N - xi_k) / Omega_k) with a
+//                          Hann H on ]-1/2, 1/2[ and flat plateaus for k = 0
+//                          and K + 1; Omega_k widened to min_filter_len bins
+//                          for k = 1..K (Sec. 5.2).
+//   eq. framecond1         M_k >= |J_k| (next power of two, at least 16).
+//   Prop. 2                d[j] = sum over all 2K+2 channels of M_k g_k[j]^2
+//                          (channels K+2..2K+1 are the mirrors g_k[-j]) and
+//                          g~_k = g_k / d, eq. painlessframe2.
+//   Sec. 4.2               Tukey transition h_0 = cos^2(pi u / 2).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "fft_common.cuh"
+#include "internal.h"
+
+namespace slicq {
+
+namespace {
+
+bool is_pow2(int64_t x) { return x > 0 && (x & (x - 1)) == 0; }
+int ilog2_64(int64_t x) {
+  int r = 0;
+  while ((int64_t(1) << r) < x) ++r;
+  return r;
+}
+
+}  // namespace
+
+slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
+  if (!p || !pl) return SLICQ_EINVAL;
+  if (!(p->fs > 0) || !(p->fmin > 0) || !(p->fmax > p->fmin) || p->bins_per_octave < 1 ||
+      p->min_filter_len < 1 || !std::isfinite(p->fs) || !std::isfinite(p->fmax))
+    return SLICQ_EINVAL;
+  if (p->window != SLICQ_WIN_HANN || p->mk_policy != SLICQ_MK_POW2) return SLICQ_EINVAL;
+  const int64_t L2 = p->slice_len;
+  if (!is_pow2(L2)) return SLICQ_EINVAL;
+  if (L2 < 2048 || L2 > 131072) return SLICQ_EUNSUPPORTED;
+  const int64_t N = L2 / 2;
+  const int64_t Mtr = p->trans_len;
+  if (Mtr < 2 || (Mtr & 1) || Mtr >= N) return SLICQ_EINVAL;
+  if (p->slice_cluster != 0 && (!is_pow2(p->slice_cluster) || p->slice_cluster > 8))
+    return SLICQ_EINVAL;
+  pl->params = *p;
+  pl->N = N;
+
+  // ---- Table 1
+  const int B = p->bins_per_octave;
+  const double Q = 1.0 / (std::pow(2.0, 1.0 / B) - std::pow(2.0, -1.0 / B));
+  int64_t K = (int64_t)std::ceil(B * std::log2(p->fmax / p->fmin) - 1e-9) + 1;
+  while (K >= 1 && p->fmin * std::pow(2.0, (double)(K - 1) / B) >= p->fs / 2) --K;
+  if (K < 1) return SLICQ_EINVAL;
+  if (K > 30000) return SLICQ_EUNSUPPORTED;
+  pl->K = (int)K;
+  const int nch = (int)K + 2;
+  pl->n_channels = nch;
+  pl->xi.assign(nch, 0.0);
+  pl->omega.assign(nch, 0.0);
+  const double floor_bw = p->min_filter_len * p->fs / (double)L2;
+  for (int k = 1; k <= K; ++k) {
+    pl->xi[k] = p->fmin * std::pow(2.0, (double)(k - 1) / B);
+    pl->omega[k] = std::max(pl->xi[k] / Q, floor_bw);
+  }
+  pl->xi[0] = 0.0;
+  pl->omega[0] = 2.0 * p->fmin;
+  pl->xi[K + 1] = p->fs / 2.0;
+  pl->omega[K + 1] = p->fs - 2.0 * pl->xi[K];
+
+  // ---- supports J_k: integers j with |(j xi_s / 2N - xi_k) / Omega_k| < 1/2
+  pl->bands.assign(nch, BandDesc{});
+  pl->jlo.assign(nch, 0);
+  int64_t coef_off = 0, win_off = 0;
+  std::vector<int> foot_lo(nch), foot_hi(nch);
+  std::vector<int32_t> cover(N + 2, 0);
+  for (int k = 0; k < nch; ++k) {
+    const double centre = pl->xi[k] * (double)L2 / p->fs;
+    const double half = pl->omega[k] * (double)L2 / (2.0 * p->fs);
+    const int64_t lo = (int64_t)std::floor(centre - half) - 1;
+    const int64_t hi = (int64_t)std::ceil(centre + half) + 1;
+    int64_t first = 0, count = 0;
+    for (int64_t j = lo; j <= hi; ++j) {
+      const double t = ((double)j * p->fs / (double)L2 - pl->xi[k]) / pl->omega[k];
+      if (std::fabs(t) < 0.5) {
+        if (count == 0) first = j;
+        if (j != first + count) return SLICQ_EINVAL;  // support must be an interval
+        ++count;
+      }
+    }
+    if (count == 0) {  // degenerate plateau: no bin; keep a zero window of one bin
+      first = (int64_t)std::llround(centre);
+    }
+    int64_t M = 16;
+    while (M < count) M <<= 1;
+    if (M > L2) return SLICQ_EINVAL;
+    if (M > (int64_t(1) << kMaxBandLog2)) return SLICQ_EUNSUPPORTED;
+    BandDesc& bd = pl->bands[k];
+    bd.j0 = (int32_t)(((first % L2) + L2) % L2);
+    bd.len = (int32_t)count;
+    bd.log2M = ilog2_64(M);
+    bd.coef_off = (int32_t)coef_off;
+    bd.win_off = (int32_t)win_off;
+    pl->jlo[k] = first;
+    coef_off += M;
+    win_off += count;
+    // footprint in the half spectrum 0..N and mirror flag
+    int flo = (int)N + 1, fhi = -1, mirror = 0;
+    for (int64_t o = 0; o < count; ++o) {
+      const int64_t b = (bd.j0 + o) % L2;
+      const int64_t h = b <= N ? b : L2 - b;
+      if (b == 0 || b == N || b > N) mirror = 1;
+      flo = std::min<int>(flo, (int)h);
+      fhi = std::max<int>(fhi, (int)h);
+      cover[h] += 1;
+    }
+    if (count == 0) { flo = fhi = (int)std::min<int64_t>(std::max<int64_t>(bd.j0 <= N ? bd.j0 : L2 - bd.j0, 0), N); }
+    bd.mirror = mirror;
+    foot_lo[k] = flo;
+    foot_hi[k] = fhi;
+  }
+  for (int64_t h = 0; h <= N; ++h)
+    if (cover[h] == 0) return SLICQ_EINVAL;  // eq. painlessframe1 fails: d[h] = 0
+  if (coef_off > (int64_t)1 << 30) return SLICQ_EUNSUPPORTED;
+  pl->coefs_per_slice = coef_off;
+  pl->win_total = win_off;
+
+  // ---- band groups: consecutive channels, <= kBandThreads threads each
+  pl->groups.clear();
+  pl->thread_band.clear();
+  int band_smem_c = 0;
+  {
+    int k = 0;
+    while (k < nch) {
+      GroupDesc gd{};
+      gd.band_begin = k;
+      int threads = 0, smem = 0;
+      while (k < nch) {
+        const int lm = pl->bands[k].log2M;
+        const int M = 1 << lm;
+        const int need_t = M >= kPerThread ? M / kPerThread : 1;
+        const int need_s = M + (M >> ((lm + 1) / 2));
+        if (threads + need_t > kBandThreads) break;
+        pl->bands[k].tofs = threads;
+        pl->bands[k].smem_off = smem;
+        threads += need_t;
+        smem += need_s;
+        ++k;
+      }
+      gd.band_end = k;
+      int alo = (int)N + 1, ahi = -1;
+      gd.any_mirror = 0;
+      for (int b = gd.band_begin; b < gd.band_end; ++b) {
+        alo = std::min(alo, foot_lo[b]);
+        ahi = std::max(ahi, foot_hi[b]);
+        gd.any_mirror |= pl->bands[b].mirror;
+      }
+      gd.acc_lo = alo;
+      gd.acc_hi = ahi + 1;
+      band_smem_c = std::max(band_smem_c, std::max(smem, gd.acc_hi - gd.acc_lo));
+      // greedy interval colouring of the footprints (in channel order)
+      std::vector<int> col_end;
+      for (int b = gd.band_begin; b < gd.band_end; ++b) {
+        int c = 0;
+        while (c < (int)col_end.size() && col_end[c] >= foot_lo[b]) ++c;
+        if (c == (int)col_end.size()) col_end.push_back(-1);
+        col_end[c] = std::max(col_end[c], foot_hi[b]);
+        pl->bands[b].color = c;
+      }
+      gd.ncolor = (int)col_end.size();
+      pl->groups.push_back(gd);
+      std::vector<int16_t> tb(kBandThreads, (int16_t)-1);
+      for (int b = gd.band_begin; b < gd.band_end; ++b) {
+        const int M = 1 << pl->bands[b].log2M;
+        const int nt = M >= kPerThread ? M / kPerThread : 1;
+        for (int i = 0; i < nt; ++i) tb[pl->bands[b].tofs + i] = (int16_t)b;
+      }
+      pl->thread_band.insert(pl->thread_band.end(), tb.begin(), tb.end());
+    }
+  }
+  const int G = (int)pl->groups.size();
+  pl->G = G;
+  // ---- boundaries between neighbouring groups
+  pl->bounds.clear();
+  pl->max_ovl = 1;
+  for (int g = 0; g < G; ++g) pl->groups[g].left_bd = pl->groups[g].right_bd = -1;
+  for (int g = 0; g + 1 < G; ++g) {
+    GroupDesc& a = pl->groups[g];
+    GroupDesc& b = pl->groups[g + 1];
+    if (b.acc_lo < a.acc_lo || b.acc_hi < a.acc_hi) return SLICQ_EUNSUPPORTED;
+    if (b.acc_lo > a.acc_hi) return SLICQ_EINVAL;  // uncovered bins
+    if (g + 2 < G && pl->groups[g + 2].acc_lo < a.acc_hi) return SLICQ_EUNSUPPORTED;
+    if (b.acc_lo < a.acc_hi) {
+      BoundaryDesc bd{b.acc_lo, a.acc_hi};
+      a.right_bd = b.left_bd = (int)pl->bounds.size();
+      pl->bounds.push_back(bd);
+      pl->max_ovl = std::max(pl->max_ovl, bd.hi - bd.lo);
+    }
+  }
+  // every boundary slot is [g][g+1] indexed by g: remap to group index
+  {
+    std::vector<BoundaryDesc> byg(std::max(G - 1, 1), BoundaryDesc{0, 0});
+    for (int g = 0; g + 1 < G; ++g) {
+      if (pl->groups[g].right_bd >= 0) byg[g] = pl->bounds[pl->groups[g].right_bd];
+      pl->groups[g].right_bd = pl->groups[g].right_bd >= 0 ? g : -1;
+      pl->groups[g + 1].left_bd = pl->groups[g].right_bd;
+    }
+    pl->bounds = byg;
+  }
+  if (pl->groups.front().acc_lo != 0 || pl->groups.back().acc_hi != N + 1) return SLICQ_EINVAL;
+  for (int g = 0; g < G; ++g) {
+    GroupDesc& gd = pl->groups[g];
+    gd.ex_lo = gd.left_bd >= 0 ? pl->bounds[gd.left_bd].hi : gd.acc_lo;
+    gd.ex_hi = gd.right_bd >= 0 ? pl->bounds[gd.right_bd].lo : gd.acc_hi;
+  }
+  pl->band_smem = band_smem_c * (int)sizeof(float2);
+  if (pl->band_smem > 200 * 1024) return SLICQ_EUNSUPPORTED;
+
+  // ---- slice FFT geometry: N = P Q, cluster of C CTAs, <= 256 threads each
+  const int logN = ilog2_64(N);
+  pl->logP = logN / 2;
+  pl->logQ = logN - pl->logP;
+  int C = p->slice_cluster;
+  if (C == 0) {
+    C = 1;
+    while (N / C > 32 * kSliceMaxThreads) C <<= 1;
+  }
+  if (N / C > 32 * kSliceMaxThreads || (1 << pl->logP) < C || N / (32 * C) < 1) return SLICQ_EUNSUPPORTED;
+  pl->C = C;
+  {
+    const int P = 1 << pl->logP, Qn = 1 << pl->logQ;
+    const int R2p = P / (1 << ((pl->logP + 1) / 2));
+    const int R2q = Qn / (1 << ((pl->logQ + 1) / 2));
+    const int cs1 = (Qn / C) * (P + R2p + 1);
+    const int xs1 = (Qn / C) * (P + 1);
+    const int cs3 = (P / C) * (Qn + R2q + 1);
+    const int zs3 = (P / C) * (Qn + 1);
+    pl->slice_smem = std::max(std::max(cs1, xs1), std::max(cs3, zs3)) * (int)sizeof(float2);
+  }
+  pl->tw_lb = (ilog2_64(L2) + 1) / 2;
+  return SLICQ_OK;
+}
+
+// ----------------------------------------------------- FP64 table kernels ---
+
+namespace {
+
+struct WinJob {
+  int64_t jlo;     // unwrapped first support sample
+  double xi, omega;
+  int32_t len, win_off, plateau, M, j0, pair;  // pair: channel has a mirror
+};
+
+__device__ double hann_or_plateau(const WinJob& w, int64_t j, double fs, double L2) {
+  if (w.plateau) return 1.0;
+  const double t = ((double)j * fs / L2 - w.xi) / w.omega;
+  if (fabs(t) >= 0.5) return 0.0;
+  const double c = cospi(t);
+  return c * c;
+}
+
+// g_k on its support, FP64
+__global__ void k_windows(const WinJob* jobs, int nch, int64_t total, double fs, double L2,
+                          double* g64) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  int lo = 0, hi = nch - 1;  // last job with win_off <= i
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (jobs[mid].win_off <= i) lo = mid; else hi = mid - 1;
+  }
+  const WinJob w = jobs[lo];
+  g64[i] = hann_or_plateau(w, w.jlo + (i - w.win_off), fs, L2);
+}
+
+// d[j] = sum_k M_k (g_k[j]^2 + [k has a mirror] g_k[-j]^2) over the circle
+__global__ void k_diagonal(const WinJob* jobs, int nch, const double* g64, int64_t L2, double* d) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= L2) return;
+  double acc = 0.0;
+  for (int k = 0; k < nch; ++k) {
+    const WinJob w = jobs[k];
+    int64_t o = j - w.j0;
+    if (o < 0) o += L2;
+    if (o < w.len) {
+      const double g = g64[w.win_off + o];
+      acc += (double)w.M * g * g;
+    }
+    if (w.pair) {
+      int64_t om = (L2 - j) % L2 - w.j0;
+      if (om < 0) om += L2;
+      if (om < w.len) {
+        const double g = g64[w.win_off + om];
+        acc += (double)w.M * g * g;
+      }
+    }
+  }
+  d[j] = acc;
+}
+
+// analysis, synthesis (dual) and adjoint tables, float32
+__global__ void k_duals(const WinJob* jobs, int nch, int64_t total, const double* g64,
+                        const double* d, int64_t L2, float* ga, float* gs, float* gadj,
+                        int* bad) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  int lo = 0, hi = nch - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) / 2;
+    if (jobs[mid].win_off <= i) lo = mid; else hi = mid - 1;
+  }
+  const WinJob w = jobs[lo];
+  const int64_t b = (w.j0 + (i - w.win_off)) % L2;
+  const double g = g64[i];
+  const double s = 1.0 / sqrt((double)L2);
+  const double dj = d[b];
+  if (!(dj > 0.0)) { *bad = 1; return; }
+  const double weight = w.pair ? 1.0 : 0.5;  // self-mirror channels 0 and K+1
+  ga[i] = (float)(g * s);
+  gs[i] = (float)(weight * g / dj * s);
+  gadj[i] = (float)(0.5 * g * s);
+}
+
+// exp(-2 pi i t / L2): fine table t < 2^lb, coarse table (t << lb)
+__global__ void k_twiddles(int64_t L2, int lb, float2* lo, float2* hi) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  const int64_t nlo = int64_t(1) << lb;
+  const int64_t nhi = L2 >> lb;
+  if (i < nlo) {
+    double s, c;
+    sincospi(-2.0 * (double)i / (double)L2, &s, &c);
+    lo[i] = make_float2((float)c, (float)s);
+  }
+  if (i < nhi) {
+    double s, c;
+    sincospi(-2.0 * (double)(i << lb) / (double)L2, &s, &c);
+    hi[i] = make_float2((float)c, (float)s);
+  }
+}
+
+// Tukey transition h_0 at |j - N| = (N - M)/2 + o, o = 0..M
+__global__ void k_tukey(int64_t M, float* hw) {
+  const int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (o > M) return;
+  const double c = cospi(0.5 * (double)o / (double)M);
+  hw[o] = (float)(c * c);
+}
+
+size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+
+}  // namespace
+
+slicq_status build_tables(slicq_plan* pl) {
+  const int nch = pl->n_channels;
+  const int64_t L2 = 2 * pl->N;
+  const int64_t Mtr = pl->params.trans_len;
+  // arena layout
+  size_t off = 0;
+  auto take = [&](size_t bytes) { const size_t o = off; off = align256(off + bytes); return o; };
+  const size_t o_bands = take(sizeof(BandDesc) * nch);
+  const size_t o_groups = take(sizeof(GroupDesc) * pl->G);
+  const size_t o_bounds = take(sizeof(BoundaryDesc) * pl->bounds.size());
+  const size_t o_tb = take(sizeof(int16_t) * pl->thread_band.size());
+  const size_t o_ga = take(sizeof(float) * std::max<int64_t>(pl->win_total, 1));
+  const size_t o_gs = take(sizeof(float) * std::max<int64_t>(pl->win_total, 1));
+  const size_t o_gadj = take(sizeof(float) * std::max<int64_t>(pl->win_total, 1));
+  const size_t o_hw = take(sizeof(float) * (Mtr + 1));
+  const size_t o_twlo = take(sizeof(float2) * (size_t(1) << pl->tw_lb));
+  const size_t o_twhi = take(sizeof(float2) * (L2 >> pl->tw_lb));
+  if (cudaMalloc(&pl->d_arena, off) != cudaSuccess) return SLICQ_ENOMEM;
+  char* base = (char*)pl->d_arena;
+  pl->d_bands = (BandDesc*)(base + o_bands);
+  pl->d_groups = (GroupDesc*)(base + o_groups);
+  pl->d_bounds = (BoundaryDesc*)(base + o_bounds);
+  pl->d_thread_band = (int16_t*)(base + o_tb);
+  pl->d_ga = (float*)(base + o_ga);
+  pl->d_gs = (float*)(base + o_gs);
+  pl->d_gadj = (float*)(base + o_gadj);
+  pl->d_hw = (float*)(base + o_hw);
+  pl->d_tw_lo = (float2*)(base + o_twlo);
+  pl->d_tw_hi = (float2*)(base + o_twhi);
+
+  slicq_status st = SLICQ_OK;
+  cudaError_t e = cudaSuccess;
+  e = cudaMemcpy(pl->d_bands, pl->bands.data(), sizeof(BandDesc) * nch, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(pl->d_groups, pl->groups.data(), sizeof(GroupDesc) * pl->G, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(pl->d_bounds, pl->bounds.data(), sizeof(BoundaryDesc) * pl->bounds.size(),
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(pl->d_thread_band, pl->thread_band.data(),
+                   sizeof(int16_t) * pl->thread_band.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return SLICQ_ECUDA;
+
+  // temporaries for the FP64 computation
+  std::vector<WinJob> jobs(nch);
+  for (int k = 0; k < nch; ++k) {
+    const BandDesc& b = pl->bands[k];
+    jobs[k] = WinJob{pl->jlo[k], pl->xi[k], pl->omega[k], b.len, b.win_off,
+                     (k == 0 || k == pl->K + 1) ? 1 : 0, 1 << b.log2M, b.j0,
+                     (k >= 1 && k <= pl->K) ? 1 : 0};
+  }
+  WinJob* d_jobs = nullptr;
+  double* d_g64 = nullptr;
+  double* d_d = nullptr;
+  int* d_bad = nullptr;
+  const int64_t wt = std::max<int64_t>(pl->win_total, 1);
+  if (cudaMalloc(&d_jobs, sizeof(WinJob) * nch) != cudaSuccess ||
+      cudaMalloc(&d_g64, sizeof(double) * wt) != cudaSuccess ||
+      cudaMalloc(&d_d, sizeof(double) * L2) != cudaSuccess ||
+      cudaMalloc(&d_bad, sizeof(int)) != cudaSuccess) {
+    st = SLICQ_ENOMEM;
+  }
+  int bad = 0;
+  if (st == SLICQ_OK) {
+    e = cudaMemcpy(d_jobs, jobs.data(), sizeof(WinJob) * nch, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemset(d_bad, 0, sizeof(int));
+    const int T = 256;
+    if (e == cudaSuccess && pl->win_total > 0) {
+      k_windows<<<(unsigned)((pl->win_total + T - 1) / T), T>>>(d_jobs, nch, pl->win_total, pl->params.fs,
+                                                                (double)L2, d_g64);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+      k_diagonal<<<(unsigned)((L2 + T - 1) / T), T>>>(d_jobs, nch, d_g64, L2, d_d);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && pl->win_total > 0) {
+      k_duals<<<(unsigned)((pl->win_total + T - 1) / T), T>>>(d_jobs, nch, pl->win_total, d_g64, d_d, L2,
+                                                              pl->d_ga, pl->d_gs, pl->d_gadj, d_bad);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+      const int64_t nt = std::max<int64_t>(int64_t(1) << pl->tw_lb, L2 >> pl->tw_lb);
+      k_twiddles<<<(unsigned)((nt + T - 1) / T), T>>>(L2, pl->tw_lb, pl->d_tw_lo, pl->d_tw_hi);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+      k_tukey<<<(unsigned)((Mtr + 1 + T - 1) / T), T>>>(Mtr, pl->d_hw);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&bad, d_bad, sizeof(int), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) st = SLICQ_ECUDA;
+    else if (bad) st = SLICQ_EINVAL;
+  }
+  cudaFree(d_jobs);
+  cudaFree(d_g64);
+  cudaFree(d_d);
+  cudaFree(d_bad);
+  return st;
+}
+
+}  // namespace slicq

@@ -1,0 +1,402 @@
+// Slice stage of the sliCQ: one thread-block cluster per slice.
+//
+// Forward (Algorithm 3, slicing, and Algorithm 1, line 2): the slice
+// f^m[j] = f[j + (m-1)N] h_0[j - N] (j < 2N, circular, zero-padded) is
+// transformed with a real-input DFT of length 2N, computed as an N-point
+// complex DFT of z[n] = f^m[2n] + i f^m[2n+1] followed by the even/odd split.
+// Bins 0..N go to the workspace for the band kernels.
+//
+// Inverse (Algorithm 2, last line, and Algorithm 4, overlap-add): bins 0..N
+// of the synthesised slice spectrum are extended Hermitian, transformed back
+// with an N-point complex DFT, multiplied by the dual slicing window
+// (indicator of the support of h_0; h_0 itself for the adjoint) and
+// overlap-added.  Samples where only this slice contributes are stored
+// directly; in each transition both slices hand their values over and the
+// second to arrive stores the sum (a + b == b + a), so the result is
+// deterministic and needs no zero-filled output.
+//
+// The N-point DFT is a four-step transform N = P Q distributed over the C
+// CTAs of the cluster: column DFTs (length P) over the CTA's Q/C columns,
+// twiddle W_N^{q u}, one exchange through distributed shared memory, row DFTs
+// (length Q) over the CTA's P/C rows; element (u, v) of the result is
+// Z[u + P v].  Each DFT is a two-pass Stockham team transform in registers.
+#include <cooperative_groups.h>
+
+#include "fft_common.cuh"
+#include "internal.h"
+
+namespace cg = cooperative_groups;
+
+namespace slicq {
+namespace {
+
+struct SliceArgs {
+  const float* __restrict__ f;    // forward input [batch][n]
+  float* out;                     // inverse output [batch][n]
+  float2* spec;                   // [slice][spec_stride]
+  int64_t spec_stride;
+  int64_t n, L;
+  int S, N, Mtr;
+  int C, logQc, logPc;
+  const float* __restrict__ hw;   // Tukey transition, Mtr + 1 values
+  TwiddleTables tw;
+  float* ola_patch;               // [slice][2][Mtr]
+  uint32_t* ola_cnt;              // [slice][C]
+  int adjoint;                    // multiply the output by h_0 instead of 1
+};
+
+// h_0 at slice sample j (reading of the Tukey window, Sec. 4.2).
+__device__ __forceinline__ float slicing_window(const SliceArgs& a, int j) {
+  const int d = abs(j - a.N);
+  const int a0 = (a.N - a.Mtr) >> 1;
+  if (d <= a0) return 1.f;
+  if (2 * d < a.N + a.Mtr) return __ldg(a.hw + (d - a0));
+  return 0.f;
+}
+
+template <int LOGP, int LOGQ>
+struct Geo {
+  static constexpr int P = 1 << LOGP, Q = 1 << LOGQ;
+  using TP = Team<LOGP>;
+  using TQ = Team<LOGQ>;
+  static constexpr int CS1 = TP::BUF + 1;  // odd column stride of pass buffers
+  static constexpr int XS1 = P + 1;        // column stride of the exchange layout
+  static constexpr int CS3 = TQ::BUF + 1;
+  static constexpr int ZS3 = Q + 1;
+};
+
+// Phase 1 + exchange + phase 3 of the distributed four-step DFT.  LOAD(e)
+// returns input element e (0 <= e < N).  On return res[i * R2q + r] holds
+// Z[u + P v] for u = rank * P/C + ul, v = (tt + TTq i) + r R1q, and the shared
+// memory may be reused after a __syncthreads().
+template <int LOGP, int LOGQ, int SIGN, class Load>
+__device__ __forceinline__ void fourstep(const SliceArgs& a, cg::cluster_group& cluster,
+                                         float2* sm, Load load, float2* res, int& ul_out,
+                                         int& tt_out) {
+  using G = Geo<LOGP, LOGQ>;
+  using TP = typename G::TP;
+  using TQ = typename G::TQ;
+  const int t = threadIdx.x;
+  const int rank = (int)cluster.block_rank();
+  const int log2N2 = LOGP + LOGQ + 1;
+
+  // ---- phase 1: column DFTs over p for the CTA's columns q
+  {
+    const int Qc = 1 << a.logQc;
+    const int ql = t & (Qc - 1);
+    const int tt = t >> a.logQc;
+    const int q = rank * Qc + ql;
+    float2* buf = sm + ql * G::CS1;
+    team_pass1<LOGP, SIGN>(tt, buf, [&](int p) { return load(p * G::Q + q); });
+    __syncthreads();
+    float2 col[TP::HELD];
+    team_pass2<LOGP, SIGN>(tt, buf, a.tw, log2N2 - LOGP, col);
+    __syncthreads();
+    // four-step twiddle W_N^{q u} = W_2N^{2 q u}, then the exchange layout [ql][u]
+#pragma unroll
+    for (int i = 0; i < TP::J2; ++i)
+#pragma unroll
+      for (int r = 0; r < TP::R2; ++r) {
+        const int u = team_out_index<LOGP>(tt, i, r);
+        float2 v = col[i * TP::R2 + r];
+        const uint32_t e = ((uint32_t)(q * u) & ((1u << (LOGP + LOGQ)) - 1u)) << 1;
+        if (e) v = c_mul(v, twiddle_s<SIGN>(a.tw, e));
+        sm[ql * G::XS1 + u] = v;
+      }
+  }
+  cluster.sync();
+
+  // ---- phase 3: row DFTs over q for the CTA's rows u
+  const int Pc = 1 << a.logPc;
+  const int ul = t & (Pc - 1);
+  const int tt = t >> a.logPc;
+  const int u = rank * Pc + ul;
+  {
+    float2 v1[TQ::J1 * TQ::R1];
+#pragma unroll
+    for (int i = 0; i < TQ::J1; ++i) {
+      const int j = tt + TQ::TT * i;
+#pragma unroll
+      for (int r = 0; r < TQ::R1; ++r) {
+        const int q = j + r * TQ::R2;
+        const int src = q >> a.logQc;
+        const int ql = q & ((1 << a.logQc) - 1);
+        const float2* rsm = cluster.map_shared_rank(sm, src);
+        v1[i * TQ::R1 + r] = rsm[ql * G::XS1 + u];
+      }
+    }
+    cluster.sync();  // every CTA has read its rows; the exchange buffer is free
+    float2* buf = sm + ul * G::CS3;
+#pragma unroll
+    for (int i = 0; i < TQ::J1; ++i) {
+      const int j = tt + TQ::TT * i;
+      float2 v[TQ::R1];
+#pragma unroll
+      for (int r = 0; r < TQ::R1; ++r) v[r] = v1[i * TQ::R1 + r];
+      dft_reg<TQ::R1, SIGN>(v);
+#pragma unroll
+      for (int r = 0; r < TQ::R1; ++r) buf[TQ::pad1(j, r)] = v[r];
+    }
+    __syncthreads();
+    team_pass2<LOGQ, SIGN>(tt, buf, a.tw, log2N2 - LOGQ, res);
+  }
+  ul_out = ul;
+  tt_out = tt;
+}
+
+// ------------------------------------------------------------- forward ---
+
+template <int LOGP, int LOGQ>
+__global__ void __launch_bounds__(kSliceMaxThreads) slice_forward_kernel(SliceArgs a) {
+  using G = Geo<LOGP, LOGQ>;
+  using TQ = typename G::TQ;
+  extern __shared__ float2 sm[];
+  cg::cluster_group cluster = cg::this_cluster();
+  const int64_t s = blockIdx.x / a.C;
+  const int64_t b = s / a.S;
+  const int m = (int)(s - b * a.S);
+  const float* f = a.f + b * a.n;
+  const int64_t base = (int64_t)(m - 1) * a.N;
+
+  auto sample = [&](int j) -> float {
+    const float w = slicing_window(a, j);
+    if (w == 0.f) return 0.f;
+    int64_t tpos = base + j;
+    if (tpos < 0) tpos += a.L;
+    if (tpos >= a.L) tpos -= a.L;
+    return tpos < a.n ? __ldg(f + tpos) * w : 0.f;
+  };
+  auto load = [&](int e) -> float2 { return make_float2(sample(2 * e), sample(2 * e + 1)); };
+
+  float2 res[TQ::HELD];
+  int ul, tt;
+  fourstep<LOGP, LOGQ, -1>(a, cluster, sm, load, res, ul, tt);
+  __syncthreads();
+  // Z rows to shared memory for the even/odd split (needs Z[N - k])
+#pragma unroll
+  for (int i = 0; i < TQ::J2; ++i)
+#pragma unroll
+    for (int r = 0; r < TQ::R2; ++r) sm[ul * G::ZS3 + team_out_index<LOGQ>(tt, i, r)] = res[i * TQ::R2 + r];
+  cluster.sync();
+
+  const int Pc = 1 << a.logPc;
+  const int rank = (int)cluster.block_rank();
+  const int u = rank * Pc + ul;
+  float2* X = a.spec + s * a.spec_stride;
+#pragma unroll
+  for (int i = 0; i < TQ::J2; ++i)
+#pragma unroll
+    for (int r = 0; r < TQ::R2; ++r) {
+      const int v = team_out_index<LOGQ>(tt, i, r);
+      const int k = u + G::P * v;
+      int up, vp;
+      if (u == 0) { up = 0; vp = (G::Q - v) & (G::Q - 1); }
+      else { up = G::P - u; vp = G::Q - 1 - v; }
+      const float2* rsm = cluster.map_shared_rank(sm, up >> a.logPc);
+      const float2 zp = c_conj(rsm[(up & (Pc - 1)) * G::ZS3 + vp]);
+      const float2 z = res[i * TQ::R2 + r];
+      // even part E = (Z[k] + conj Z[N-k]) / 2, odd part O = (Z[k] - conj Z[N-k]) / 2i
+      const float2 E = c_scale(c_add(z, zp), 0.5f);
+      const float2 D = c_sub(z, zp);
+      const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);
+      X[k] = c_add(E, c_mul(twiddle(a.tw, (uint32_t)k), O));
+      if (k == 0) X[a.N] = c_sub(E, O);
+    }
+  cluster.sync();  // keep this CTA's shared memory alive for its neighbours
+}
+
+// ------------------------------------------------------------- inverse ---
+
+// Hand one transition over or, as the second arriver, store the sum.
+// EACH(fn) calls fn(o, tpos, value) for every sample of the transition that
+// this CTA holds.
+template <class Each>
+__device__ __forceinline__ void ola_combine(const SliceArgs& a, int64_t tr_slot, int side,
+                                            int rank, int* s_flag, float* out, Each each) {
+  float* mine = a.ola_patch + (tr_slot * 2 + side) * (int64_t)a.Mtr;
+  const float* other = a.ola_patch + (tr_slot * 2 + (1 - side)) * (int64_t)a.Mtr;
+  each([&](int o, int64_t tpos, float v) { mine[o] = v; });
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned old = atomicInc(a.ola_cnt + tr_slot * a.C + rank, 1u);
+    *s_flag = (old == 1u);
+  }
+  __syncthreads();
+  if (*s_flag) {
+    __threadfence();
+    each([&](int o, int64_t tpos, float v) {
+      if (tpos < a.n) out[tpos] = v + __ldcg(other + o);
+    });
+  }
+  __syncthreads();
+}
+
+template <int LOGP, int LOGQ>
+__global__ void __launch_bounds__(kSliceMaxThreads) slice_inverse_kernel(SliceArgs a) {
+  using G = Geo<LOGP, LOGQ>;
+  using TQ = typename G::TQ;
+  extern __shared__ float2 sm[];
+  __shared__ int s_flag;
+  cg::cluster_group cluster = cg::this_cluster();
+  const int64_t s = blockIdx.x / a.C;
+  const int64_t b = s / a.S;
+  const int m = (int)(s - b * a.S);
+  const float2* H = a.spec + s * a.spec_stride;
+  const int N = a.N;
+
+  // Z[k] = (H[k] + conj H[N-k]) + i e^{+2 pi i k / 2N} (H[k] - conj H[N-k])
+  auto load = [&](int k) -> float2 {
+    const float2 h = H[k];
+    const float2 hc = c_conj(H[N - k]);
+    const float2 sum = c_add(h, hc);
+    const float2 dif = c_mul(c_sub(h, hc), twiddle_s<+1>(a.tw, (uint32_t)k));
+    return make_float2(sum.x - dif.y, sum.y + dif.x);
+  };
+
+  {
+    float2 res[TQ::HELD];
+    int ul, tt;
+    fourstep<LOGP, LOGQ, +1>(a, cluster, sm, load, res, ul, tt);
+    __syncthreads();
+#pragma unroll
+    for (int i = 0; i < TQ::J2; ++i)
+#pragma unroll
+      for (int r = 0; r < TQ::R2; ++r) sm[ul * G::ZS3 + team_out_index<LOGQ>(tt, i, r)] = res[i * TQ::R2 + r];
+  }
+  __syncthreads();
+
+  // time samples 2n, 2n+1 with n = u + P v; this CTA holds u in [rank Pc, (rank+1) Pc)
+  const int Pc = 1 << a.logPc;
+  const int rank = (int)cluster.block_rank();
+  const int a0 = (N - a.Mtr) >> 1;
+  const int64_t base = (int64_t)(m - 1) * N;
+  float* out = a.out + b * a.n;
+  const int held = Pc * G::Q;
+  auto tpos_of = [&](int j) -> int64_t {
+    int64_t tp = base + j;
+    if (tp < 0) tp += a.L;
+    if (tp >= a.L) tp -= a.L;
+    return tp;
+  };
+  auto sample = [&](int idx, int h, int& j) -> float {
+    const int ul = idx & (Pc - 1);
+    const int v = idx >> a.logPc;
+    const float2 z = sm[ul * G::ZS3 + v];
+    j = 2 * (rank * Pc + ul + G::P * v) + h;
+    const float x = h ? z.y : z.x;
+    return a.adjoint ? x * slicing_window(a, j) : x;
+  };
+
+  // samples where only this slice contributes
+  for (int idx = threadIdx.x; idx < held; idx += blockDim.x)
+    for (int h = 0; h < 2; ++h) {
+      int j;
+      const float x = sample(idx, h, j);
+      if (abs(j - N) <= a0) {
+        const int64_t tp = tpos_of(j);
+        if (tp < a.n) out[tp] = x;
+      }
+    }
+
+  // right transition (shared with slice m+1; this slice is side 0) and left
+  // transition (shared with slice m-1; side 1), offsets o in [1, M-1]
+  auto each_right = [&](auto&& fn) {
+    for (int idx = threadIdx.x; idx < held; idx += blockDim.x)
+      for (int h = 0; h < 2; ++h) {
+        int j;
+        const float x = sample(idx, h, j);
+        const int d = j - N;
+        if (d > a0 && 2 * d < N + a.Mtr) fn(d - a0, tpos_of(j), x);
+      }
+  };
+  auto each_left = [&](auto&& fn) {
+    for (int idx = threadIdx.x; idx < held; idx += blockDim.x)
+      for (int h = 0; h < 2; ++h) {
+        int j;
+        const float x = sample(idx, h, j);
+        const int d = N - j;
+        if (d > a0 && 2 * d < N + a.Mtr) fn(j - a0, tpos_of(j), x);
+      }
+  };
+  const int64_t bS = b * a.S;
+  ola_combine(a, bS + m, 0, rank, &s_flag, out, each_right);
+  ola_combine(a, bS + (m + a.S - 1) % a.S, 1, rank, &s_flag, out, each_left);
+  // no remote shared-memory access after the exchange inside fourstep()
+}
+
+template <int LOGP, int LOGQ>
+cudaError_t launch_slice(bool forward, const slicq_plan* pl, const SliceArgs& a, int64_t slices,
+                         cudaStream_t st) {
+  void (*kern)(SliceArgs) = forward ? slice_forward_kernel<LOGP, LOGQ> : slice_inverse_kernel<LOGP, LOGQ>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, pl->slice_smem);
+  if (e != cudaSuccess) return e;
+  const int threads = (1 << (LOGP + LOGQ)) / (32 * pl->C);
+  cudaLaunchConfig_t cfg{};
+  cfg.gridDim = dim3((unsigned)(slices * pl->C));
+  cfg.blockDim = dim3(threads);
+  cfg.dynamicSmemBytes = pl->slice_smem;
+  cfg.stream = st;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = pl->C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, kern, a);
+  if (e != cudaSuccess) return e;
+  return cudaGetLastError();
+}
+
+cudaError_t dispatch(bool forward, const slicq_plan* pl, const SliceArgs& a, int64_t slices,
+                     cudaStream_t st) {
+  switch (pl->logP * 16 + pl->logQ) {
+    case 5 * 16 + 5: return launch_slice<5, 5>(forward, pl, a, slices, st);
+    case 5 * 16 + 6: return launch_slice<5, 6>(forward, pl, a, slices, st);
+    case 6 * 16 + 6: return launch_slice<6, 6>(forward, pl, a, slices, st);
+    case 6 * 16 + 7: return launch_slice<6, 7>(forward, pl, a, slices, st);
+    case 7 * 16 + 7: return launch_slice<7, 7>(forward, pl, a, slices, st);
+    case 7 * 16 + 8: return launch_slice<7, 8>(forward, pl, a, slices, st);
+    case 8 * 16 + 8: return launch_slice<8, 8>(forward, pl, a, slices, st);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+SliceArgs make_args(const slicq_plan* pl, const Workspace& ws, int64_t n) {
+  SliceArgs a{};
+  a.spec = ws.spec;
+  a.spec_stride = ws.spec_stride;
+  a.n = n;
+  a.L = ws.L;
+  a.S = (int)ws.S;
+  a.N = (int)pl->N;
+  a.Mtr = (int)pl->params.trans_len;
+  a.C = pl->C;
+  a.logQc = pl->logQ - ilog2c(pl->C);
+  a.logPc = pl->logP - ilog2c(pl->C);
+  a.hw = pl->d_hw;
+  a.tw = TwiddleTables{pl->d_tw_lo, pl->d_tw_hi, pl->tw_lb};
+  a.ola_patch = ws.ola_patch;
+  a.ola_cnt = ws.ola_cnt;
+  return a;
+}
+
+}  // namespace
+
+cudaError_t launch_slice_forward(const slicq_plan* pl, const float* f, int64_t n, int64_t batch,
+                                 const Workspace& ws, cudaStream_t st) {
+  SliceArgs a = make_args(pl, ws, n);
+  a.f = f;
+  return dispatch(true, pl, a, batch * ws.S, st);
+}
+
+cudaError_t launch_slice_inverse(const slicq_plan* pl, int64_t n, int64_t batch, SynthKind kind,
+                                 const Workspace& ws, float* out, cudaStream_t st) {
+  SliceArgs a = make_args(pl, ws, n);
+  a.out = out;
+  a.adjoint = kind == kSynthAdjoint;
+  return dispatch(false, pl, a, batch * ws.S, st);
+}
+
+}  // namespace slicq

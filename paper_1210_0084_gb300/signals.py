@@ -73,12 +73,18 @@ def pink_noise_harmonic_tones(n: int, fs: float, channels: int, seed: int,
             tau = rng.uniform(*tau_range)
             onset = rng.uniform(0.0, n / fs)
             amp = rng.uniform(0.05, 0.2)
-            env = np.where(t >= onset, np.exp(-(t - onset) / tau), 0.0)
             ph = rng.uniform(0.0, 2.0 * np.pi, partials)
+            # the envelope is below 1e-7 after 16 tau: evaluate the active span only
+            i0 = int(np.ceil(onset * fs))
+            i1 = min(n, i0 + int(16.0 * tau * fs) + 1)
+            if i0 >= n:
+                continue
+            ts = t[i0:i1]
+            env = np.exp(-(ts - onset) / tau)
             for kk in range(1, partials + 1):
                 if kk * f0 >= fs / 2:
                     break
-                x += amp / kk * env * np.sin(2.0 * np.pi * kk * f0 * t + ph[kk - 1])
+                x[i0:i1] += amp / kk * env * np.sin(2.0 * np.pi * kk * f0 * ts + ph[kk - 1])
         out[c] = x
     return out
 

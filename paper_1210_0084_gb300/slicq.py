@@ -1,0 +1,308 @@
+"""Python binding of libslicq (argument marshalling only).
+
+Every step of the transform runs in the library's CUDA kernels; this module
+only checks shapes and dtypes, allocates outputs and workspaces with PyTorch
+and passes raw pointers and the current CUDA stream through the C ABI of
+``include/slicq.h``.  Importing it loads ``lib/libslicq.so`` and raises if the
+library is missing: there is no fallback implementation.
+
+    plan = SliCQPlan(SliCQParams(fs=44100, fmin=32.7, fmax=22050,
+                                 bins_per_octave=48, slice_len=65536,
+                                 trans_len=16384))
+    c = plan.forward(x)          # x: float32 [batch, n] on the GPU
+    y = plan.inverse(c, n)       # perfect reconstruction (Prop. 3)
+    g = plan.adjoint(c, n)       # Re(A^H c), the gradient of the analysis
+
+Citations: Holighaus, Doerfler, Velasco, Grill, arXiv:1210.0084 —
+Algorithms 1-4, Proposition 2 (dual windows), Table 1 (channel layout).
+"""
+
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Dict, Optional, Tuple
+
+import numpy as np
+
+__all__ = [
+    "SliCQParams", "SliCQPlan", "SliCQError", "SliCQFunction", "slicq_transform",
+    "layout", "lib_path", "load_library", "STATUS",
+]
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+STATUS = {0: "SLICQ_OK", 1: "SLICQ_EINVAL", 2: "SLICQ_ENOMEM", 3: "SLICQ_ECUDA",
+          4: "SLICQ_ESIZE", 5: "SLICQ_ETIMEOUT", 6: "SLICQ_EUNSUPPORTED"}
+
+
+def lib_path() -> str:
+    return os.environ.get("SLICQ_LIB", os.path.join(_PKG, "lib", "libslicq.so"))
+
+
+class SliCQError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: {STATUS.get(status, status)}")
+        self.status = status
+
+
+class _Params(ctypes.Structure):
+    _fields_ = [("fs", ctypes.c_double), ("fmin", ctypes.c_double), ("fmax", ctypes.c_double),
+                ("bins_per_octave", ctypes.c_int32), ("min_filter_len", ctypes.c_int32),
+                ("slice_len", ctypes.c_int64), ("trans_len", ctypes.c_int64),
+                ("window", ctypes.c_int32), ("mk_policy", ctypes.c_int32),
+                ("slice_cluster", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load_library():
+    """Load libslicq.so once (raises OSError if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        raise OSError(f"libslicq.so not built at {path}; run "
+                      "`python -m paper_1210_0084_gb300.build`")
+    L = ctypes.CDLL(path)
+    P, I32, I64, VP, SZ = (ctypes.POINTER(_Params), ctypes.c_int32, ctypes.c_int64,
+                           ctypes.c_void_p, ctypes.c_size_t)
+    sig = {
+        "slicq_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "slicq_abi_version": (I32, []),
+        "slicq_layout": (ctypes.c_int, [P, ctypes.POINTER(I32), ctypes.POINTER(I64)]),
+        "slicq_layout_tables": (ctypes.c_int, [P, I32, VP, VP, VP, VP, VP, VP]),
+        "slicq_plan_create": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(VP)]),
+        "slicq_plan_destroy": (None, [VP]),
+        "slicq_plan_info": (ctypes.c_int, [VP, ctypes.POINTER(I32), ctypes.POINTER(I64)]),
+        "slicq_num_slices": (I64, [VP, I64]),
+        "slicq_workspace_size": (ctypes.c_int, [VP, I64, I64, ctypes.POINTER(SZ)]),
+        "slicq_forward": (ctypes.c_int, [VP, VP, I64, I64, VP, I64, VP, SZ, VP]),
+        "slicq_inverse": (ctypes.c_int, [VP, VP, I64, I64, VP, VP, SZ, VP]),
+        "slicq_adjoint": (ctypes.c_int, [VP, VP, I64, I64, VP, VP, SZ, VP]),
+        "slicq_plan_table": (ctypes.c_int, [VP, I32, VP, I64, ctypes.POINTER(I64)]),
+        "slicq_trace_enable": (ctypes.c_int, [VP, I32]),
+        "slicq_trace_read": (ctypes.c_int, [VP, VP, VP, I32, ctypes.POINTER(I32)]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status: int, what: str):
+    if status != 0:
+        raise SliCQError(status, what)
+
+
+@dataclass(frozen=True)
+class SliCQParams:
+    """Parameters of one sliCQ system (Table 1 and Sec. 4; see slicq.h)."""
+
+    fs: float
+    fmin: float
+    fmax: float
+    bins_per_octave: int
+    slice_len: int
+    trans_len: int
+    min_filter_len: int = 16
+    slice_cluster: int = 0
+
+    def to_c(self) -> _Params:
+        return _Params(float(self.fs), float(self.fmin), float(self.fmax),
+                       int(self.bins_per_octave), int(self.min_filter_len),
+                       int(self.slice_len), int(self.trans_len), 0, 0,
+                       int(self.slice_cluster), 0)
+
+
+def layout(p: SliCQParams) -> Dict[str, np.ndarray]:
+    """Host-only channel layout (no GPU): M, off, j0, len, xi, omega per channel."""
+    L = load_library()
+    cp = p.to_c()
+    nch = ctypes.c_int32()
+    cps = ctypes.c_int64()
+    _check(L.slicq_layout(ctypes.byref(cp), ctypes.byref(nch), ctypes.byref(cps)), "slicq_layout")
+    n = nch.value
+    out = {"M": np.zeros(n, np.int32), "off": np.zeros(n, np.int64), "j0": np.zeros(n, np.int64),
+           "len": np.zeros(n, np.int32), "xi": np.zeros(n, np.float64),
+           "omega": np.zeros(n, np.float64)}
+    _check(L.slicq_layout_tables(ctypes.byref(cp), n, *(out[k].ctypes.data for k in
+                                                         ("M", "off", "j0", "len", "xi", "omega"))),
+           "slicq_layout_tables")
+    out["coefs_per_slice"] = int(cps.value)
+    return out
+
+
+class SliCQPlan:
+    """A plan on one CUDA device: channel layout and FP64-derived tables."""
+
+    def __init__(self, params: SliCQParams, device: Optional[int] = None):
+        import torch
+        self._torch = torch
+        self.params = params
+        self.lib = load_library()
+        self.device = torch.cuda.current_device() if device is None else int(device)
+        h = ctypes.c_void_p()
+        cp = params.to_c()
+        _check(self.lib.slicq_plan_create(ctypes.byref(cp), self.device, ctypes.byref(h)),
+               "slicq_plan_create")
+        self._h = h
+        nch = ctypes.c_int32()
+        cps = ctypes.c_int64()
+        _check(self.lib.slicq_plan_info(h, ctypes.byref(nch), ctypes.byref(cps)), "slicq_plan_info")
+        self.n_channels = nch.value
+        self.coefs_per_slice = cps.value
+        self._work: Dict[Tuple[int, int], "torch.Tensor"] = {}
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                self.lib.slicq_plan_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    # ------------------------------------------------------------------ info
+    @property
+    def handle(self) -> ctypes.c_void_p:
+        return self._h
+
+    def num_slices(self, n: int) -> int:
+        return int(self.lib.slicq_num_slices(self._h, int(n)))
+
+    def workspace_bytes(self, n: int, batch: int) -> int:
+        sz = ctypes.c_size_t()
+        _check(self.lib.slicq_workspace_size(self._h, int(n), int(batch), ctypes.byref(sz)),
+               "slicq_workspace_size")
+        return sz.value
+
+    def workspace(self, n: int, batch: int):
+        """Zero-filled device workspace for (n, batch), cached on the plan."""
+        key = (int(n), int(batch))
+        w = self._work.get(key)
+        if w is None:
+            nb = self.workspace_bytes(n, batch)
+            w = self._torch.zeros(max(nb, 256), dtype=self._torch.uint8,
+                                  device=f"cuda:{self.device}")
+            self._work[key] = w
+        return w
+
+    def table(self, which: int) -> np.ndarray:
+        """Copy of a plan table (0 analysis, 1 synthesis, 2 adjoint windows, 3 Tukey)."""
+        cap = 1 << 26
+        buf = np.zeros(cap, np.float32)
+        n = ctypes.c_int64()
+        _check(self.lib.slicq_plan_table(self._h, int(which), buf.ctypes.data, cap, ctypes.byref(n)),
+               "slicq_plan_table")
+        return buf[: n.value].copy()
+
+    KERNEL_NAMES = ("slice_forward", "band_analysis", "band_synthesis", "slice_inverse")
+
+    def trace(self, enable: bool = True):
+        """Start (or stop) recording CUDA events around every kernel launch."""
+        _check(self.lib.slicq_trace_enable(self._h, 1 if enable else 0), "slicq_trace_enable")
+
+    def trace_read(self, cap: int = 4096):
+        """[(kernel name, ms)] of the launches traced since the last read."""
+        kid = np.zeros(cap, np.int32)
+        ms = np.zeros(cap, np.float32)
+        n = ctypes.c_int32()
+        _check(self.lib.slicq_trace_read(self._h, kid.ctypes.data, ms.ctypes.data, cap,
+                                         ctypes.byref(n)), "slicq_trace_read")
+        return [(self.KERNEL_NAMES[k], float(t)) for k, t in zip(kid[: n.value], ms[: n.value])]
+
+    # ------------------------------------------------------------ transforms
+    def _stream(self):
+        return ctypes.c_void_p(self._torch.cuda.current_stream(self.device).cuda_stream)
+
+    def _as_batch(self, x):
+        t = self._torch
+        if x.dtype != t.float32 or not x.is_cuda:
+            raise TypeError("expected a float32 CUDA tensor")
+        squeeze = x.dim() == 1
+        x2 = x.reshape(1, -1) if squeeze else x
+        if x2.dim() != 2:
+            raise ValueError("expected [n] or [batch, n]")
+        return x2.contiguous(), squeeze
+
+    def forward(self, x, out=None):
+        """Coefficients complex64 [batch, S, coefs_per_slice] (Algorithm 3)."""
+        t = self._torch
+        x2, squeeze = self._as_batch(x)
+        batch, n = x2.shape
+        S = self.num_slices(n)
+        if out is None:
+            out = t.empty((batch, S, self.coefs_per_slice), dtype=t.complex64, device=x2.device)
+        w = self.workspace(n, batch)
+        _check(self.lib.slicq_forward(self._h, x2.data_ptr(), n, batch, out.data_ptr(), out.numel(),
+                                      w.data_ptr(), w.numel(), self._stream()), "slicq_forward")
+        return out[0] if squeeze else out
+
+    def _synth(self, fn, c, n, out, what):
+        t = self._torch
+        if c.dtype != t.complex64 or not c.is_cuda:
+            raise TypeError("expected complex64 CUDA coefficients")
+        squeeze = c.dim() == 2
+        c3 = c.unsqueeze(0) if squeeze else c
+        batch = c3.shape[0]
+        S = self.num_slices(n)
+        if tuple(c3.shape[1:]) != (S, self.coefs_per_slice):
+            raise ValueError(f"coefficients must be [batch, {S}, {self.coefs_per_slice}]")
+        c3 = c3.contiguous()
+        if out is None:
+            out = t.empty((batch, n), dtype=t.float32, device=c3.device)
+        w = self.workspace(n, batch)
+        _check(fn(self._h, c3.data_ptr(), int(n), batch, out.data_ptr(), w.data_ptr(), w.numel(),
+                  self._stream()), what)
+        return out[0] if squeeze else out
+
+    def inverse(self, c, n: int, out=None):
+        """Real signal [batch, n] from coefficients (Algorithm 4, canonical dual)."""
+        return self._synth(self.lib.slicq_inverse, c, n, out, "slicq_inverse")
+
+    def adjoint(self, c, n: int, out=None):
+        """Re(A^H c) [batch, n]: the gradient of the analysis map."""
+        return self._synth(self.lib.slicq_adjoint, c, n, out, "slicq_adjoint")
+
+
+def _autograd():
+    import torch
+
+    class _SliCQFunction(torch.autograd.Function):
+        """Forward sliCQ with the hand-written adjoint kernel as its backward."""
+
+        @staticmethod
+        def forward(ctx, x, plan: SliCQPlan):
+            ctx.plan = plan
+            ctx.n = x.shape[-1]
+            ctx.shape = x.shape
+            return plan.forward(x)
+
+        @staticmethod
+        def backward(ctx, grad_c):
+            g = ctx.plan.adjoint(grad_c.contiguous(), ctx.n)
+            return g.reshape(ctx.shape), None
+
+    return _SliCQFunction
+
+
+_FN = None
+
+
+def SliCQFunction():
+    """The torch.autograd.Function class (created lazily so that importing this
+    module does not import torch)."""
+    global _FN
+    if _FN is None:
+        _FN = _autograd()
+    return _FN
+
+
+def slicq_transform(x, plan: SliCQPlan):
+    """Differentiable forward sliCQ of a float32 CUDA tensor [batch, n]."""
+    return SliCQFunction().apply(x, plan)

@@ -1,0 +1,93 @@
+"""CPU tests of the C ABI: the library loads, exports every declared symbol,
+and its host-only layout (Table 1 supports, M_k, offsets) equals the
+oracle's, bit for bit.  No compute call touches a device here."""
+
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1210_0084_gb300 import build as B
+from paper_1210_0084_gb300 import slicq as S
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return S.load_library()
+
+
+def _declared_symbols(repo_root):
+    txt = open(os.path.join(repo_root, "include", "slicq.h")).read()
+    return sorted(set(re.findall(r"SLICQ_API[^;(]*?\b(slicq_\w+)\s*\(", txt)))
+
+
+def test_exports_every_declared_symbol(lib, repo_root):
+    names = _declared_symbols(repo_root)
+    assert len(names) >= 12
+    for n in names:
+        assert hasattr(lib, n), n
+    assert lib.slicq_abi_version() == 1
+
+
+def test_status_strings(lib):
+    for code, name in S.STATUS.items():
+        assert lib.slicq_status_string(code).decode().startswith(name)
+
+
+CASES = [
+    S.SliCQParams(44100.0, 50.0, 22050.0, 12, 8192, 2048),
+    S.SliCQParams(44100.0, 32.7, 22050.0, 48, 65536, 16384),
+    S.SliCQParams(48000.0, 27.5, 24000.0, 96, 131072, 32768),
+    S.SliCQParams(16000.0, 50.0, 8000.0, 96, 16384, 4096),
+    S.SliCQParams(48000.0, 50.0, 22000.0, 12, 16384, 4096),
+    S.SliCQParams(22050.0, 50.0, 11025.0, 24, 16384, 4096),
+    S.SliCQParams(44100.0, 40.0, 22050.0, 24, 8192, 2048),
+    S.SliCQParams(16000.0, 50.0, 8000.0, 24, 2048, 512),
+]
+
+
+@pytest.mark.parametrize("p", CASES, ids=lambda p: f"fs{int(p.fs)}_B{p.bins_per_octave}_L{p.slice_len}")
+def test_host_layout_matches_oracle(lib, p):
+    lay = S.layout(p)
+    op = O.make_plan(O.SliCQParams(p.fs, p.fmin, p.fmax, p.bins_per_octave, p.slice_len,
+                                   p.trans_len, p.min_filter_len))
+    K = op.K
+    assert lay["M"].shape[0] == K + 2
+    chans = op.sys.channels[: K + 2]
+    np.testing.assert_array_equal(lay["M"], [c.M for c in chans])
+    np.testing.assert_array_equal(lay["len"], [c.length for c in chans])
+    np.testing.assert_array_equal(lay["j0"], [c.j0 for c in chans])
+    np.testing.assert_array_equal(lay["off"], op.offsets)
+    np.testing.assert_allclose(lay["xi"], op.sys.xi[: K + 2], rtol=1e-13)
+    np.testing.assert_allclose(lay["omega"], op.sys.Omega[: K + 2], rtol=1e-13)
+    assert lay["coefs_per_slice"] == op.coefs_per_slice
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(fmin=0.0), 1), (dict(fmax=10.0), 1), (dict(slice_len=6000), 1),
+    (dict(trans_len=3), 1), (dict(trans_len=8192), 1), (dict(bins_per_octave=0), 1),
+    (dict(slice_len=1024, trans_len=256), 6), (dict(slice_cluster=3), 1),
+    (dict(fmin=23000.0, fmax=30000.0), 1),
+])
+def test_invalid_parameters_are_rejected(lib, kw, code):
+    base = dict(fs=44100.0, fmin=50.0, fmax=22050.0, bins_per_octave=12, slice_len=8192,
+                trans_len=2048)
+    base.update(kw)
+    p = S.SliCQParams(**base)
+    cp = p.to_c()
+    n = ctypes.c_int32()
+    c = ctypes.c_int64()
+    assert lib.slicq_layout(ctypes.byref(cp), ctypes.byref(n), ctypes.byref(c)) == code
+
+
+def test_null_pointers(lib):
+    assert lib.slicq_layout(None, None, None) == 1
+    assert lib.slicq_plan_info(None, None, None) == 1
+    assert lib.slicq_num_slices(None, 100) == 0
+    assert lib.slicq_forward(None, None, 1, 1, None, 0, None, 0, None) == 1
+    assert lib.slicq_inverse(None, None, 1, 1, None, None, 0, None) == 1
+    assert lib.slicq_adjoint(None, None, 1, 1, None, None, 0, None) == 1

@@ -1,0 +1,214 @@
+"""GPU parity of the CUDA path against the FP64 oracle, through the C ABI.
+
+Tolerances follow from float32 arithmetic: each output is a sum over a
+radix-2 FFT of length 2N (log2(2N) <= 17 stages) and a band FFT of length
+M_k (<= 10 stages) with twiddles rounded once from FP64, so the relative L2
+error is a small multiple of u * (log2(2N) + log2(M_k)) with
+u = 2^-24 ~ 6e-8, i.e. about 2e-6.  The tests require
+   coefficient, reconstruction and adjoint relative L2 error <= 1e-5
+   (the reconstruction bound is the target accuracy of the method),
+   per-element |error| <= 2e-5 * max|reference| per slice.
+"""
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1210_0084_gb300 import signals
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+REL = 1e-5
+ELEM = 2e-5
+
+
+@pytest.fixture(scope="module")
+def S():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1210_0084_gb300 import slicq
+    return slicq
+
+
+def _oplan(p):
+    return O.make_plan(O.SliCQParams(p.fs, p.fmin, p.fmax, p.bins_per_octave, p.slice_len,
+                                     p.trans_len, p.min_filter_len))
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def _check_coefs(got, ref):
+    assert got.shape == ref.shape
+    assert _rel(got, ref) <= REL, _rel(got, ref)
+    for m in range(ref.shape[0]):
+        scale = np.abs(ref[m]).max()
+        assert np.abs(got[m] - ref[m]).max() <= ELEM * scale + 1e-30, m
+
+
+SMALL = [
+    # (fs, fmin, fmax, B, 2N, M, n, batch)
+    (16000.0, 50.0, 8000.0, 24, 2048, 512, 5000, 2),       # smallest slice, ragged
+    (44100.0, 50.0, 22050.0, 12, 4096, 1024, 20000, 1),
+    (44100.0, 50.0, 22050.0, 12, 8192, 2048, 65536, 1),    # exact multiple: circular wrap
+    (16000.0, 50.0, 8000.0, 96, 16384, 4096, 40000, 1),    # many tiny bands
+    (48000.0, 50.0, 22000.0, 12, 16384, 4096, 30001, 3),   # big Nyquist plateau, odd n
+    (44100.0, 32.7, 22050.0, 48, 65536, 16384, 150000, 1), # bench plan, cluster of 4
+    (16000.0, 50.0, 8000.0, 24, 2048, 512, 1500, 1),       # n < 2N: two slices
+]
+
+
+def _params(S, c):
+    fs, fmin, fmax, B, L2, M, n, batch = c
+    return S.SliCQParams(fs, fmin, fmax, B, L2, M), n, batch
+
+
+def _signal(n, fs, batch, seed):
+    return np.stack([signals.noise_plus_sines(n, fs, seed + i) for i in range(batch)])
+
+
+@pytest.mark.parametrize("case", SMALL, ids=lambda c: f"L{c[4]}_B{c[3]}_n{c[6]}x{c[7]}")
+def test_forward_inverse_adjoint_parity(S, case):
+    p, n, batch = _params(S, case)
+    plan = S.SliCQPlan(p)
+    op = _oplan(p)
+    x = _signal(n, p.fs, batch, 100)
+    xd = torch.from_numpy(x).cuda()
+    c = plan.forward(xd)
+    y = plan.inverse(c, n)
+    torch.cuda.synchronize()
+    cg = c.cpu().numpy().astype(np.complex128)
+    for b in range(batch):
+        ref = O.slicq_forward(x[b].astype(np.float64), op)
+        _check_coefs(cg[b], ref)
+        # inverse from the GPU's own coefficients: perfect reconstruction
+        assert _rel(y[b].cpu().numpy(), x[b]) <= REL
+    # inverse and adjoint of coefficients that do not come from a real
+    # signal (modified coefficients): compared with the oracle on the same input
+    rng = np.random.default_rng(5)
+    cr = (rng.standard_normal(cg.shape) + 1j * rng.standard_normal(cg.shape)).astype(np.complex64)
+    crd = torch.from_numpy(cr).cuda()
+    yi = plan.inverse(crd, n).cpu().numpy()
+    ya = plan.adjoint(crd, n).cpu().numpy()
+    for b in range(batch):
+        ri = O.slicq_inverse(cr[b].astype(np.complex128), op, n)
+        ra = O.slicq_adjoint(cr[b].astype(np.complex128), op, n)
+        assert _rel(yi[b], ri) <= REL
+        assert _rel(ya[b], ra) <= REL
+        assert np.abs(yi[b] - ri).max() <= ELEM * np.abs(ri).max()
+        assert np.abs(ya[b] - ra).max() <= ELEM * np.abs(ra).max()
+
+
+def test_plan_tables_match_oracle(S):
+    p = S.SliCQParams(44100.0, 32.7, 22050.0, 48, 65536, 16384)
+    plan = S.SliCQPlan(p)
+    op = _oplan(p)
+    K = op.K
+    sc = 1.0 / np.sqrt(p.slice_len)
+    ga = np.concatenate([ch.g for ch in op.sys.channels[:K + 2]]) * sc
+    w = np.array([0.5 if k in (0, K + 1) else 1.0 for k in range(K + 2)])
+    gs = np.concatenate([op.dual.channels[k].g * w[k] for k in range(K + 2)]) * sc
+    np.testing.assert_allclose(plan.table(0), ga, rtol=2e-7, atol=1e-12)
+    np.testing.assert_allclose(plan.table(1), gs, rtol=2e-7, atol=1e-16)
+    np.testing.assert_allclose(plan.table(2), 0.5 * ga, rtol=2e-7, atol=1e-12)
+    N, M = p.slice_len // 2, p.trans_len
+    a0 = (N - M) // 2
+    hw = op.h0[N + a0: N + a0 + M]
+    np.testing.assert_allclose(plan.table(3)[:M], hw, rtol=2e-7, atol=1e-12)
+
+
+def test_deterministic(S):
+    p = S.SliCQParams(44100.0, 50.0, 22050.0, 12, 8192, 2048)
+    plan = S.SliCQPlan(p)
+    x = torch.from_numpy(_signal(50000, p.fs, 2, 7)).cuda()
+    c1 = plan.forward(x).clone()
+    y1 = plan.inverse(c1, 50000).clone()
+    c2 = plan.forward(x)
+    y2 = plan.inverse(c2, 50000)
+    assert torch.equal(c1, c2) and torch.equal(y1, y2)
+
+
+def test_buffer_errors(S):
+    p = S.SliCQParams(44100.0, 50.0, 22050.0, 12, 8192, 2048)
+    plan = S.SliCQPlan(p)
+    n = 20000
+    x = torch.zeros(n, device="cuda")
+    Sn = plan.num_slices(n)
+    small = torch.empty((Sn, plan.coefs_per_slice - 1), dtype=torch.complex64, device="cuda")
+    w = plan.workspace(n, 1)
+    lib = plan.lib
+    st = lib.slicq_forward(plan.handle, x.data_ptr(), n, 1, small.data_ptr(), small.numel(),
+                           w.data_ptr(), w.numel(), None)
+    assert st == 4  # SLICQ_ESIZE
+    c = torch.empty((Sn, plan.coefs_per_slice), dtype=torch.complex64, device="cuda")
+    st = lib.slicq_forward(plan.handle, x.data_ptr(), n, 1, c.data_ptr(), c.numel(),
+                           w.data_ptr(), 16, None)
+    assert st == 4
+    st = lib.slicq_forward(plan.handle, x.data_ptr(), 0, 1, c.data_ptr(), c.numel(),
+                           w.data_ptr(), w.numel(), None)
+    assert st == 1
+
+
+def _sampled_full_size(S, p, x, slices_to_check):
+    """Forward + inverse at full size on the GPU; oracle on sampled slices."""
+    plan = S.SliCQPlan(p)
+    op = _oplan(p)
+    batch, n = x.shape
+    xd = torch.from_numpy(x).cuda()
+    c = plan.forward(xd)
+    y = plan.inverse(c, n)
+    torch.cuda.synchronize()
+    for b in range(batch):
+        assert _rel(y[b].cpu().numpy(), x[b]) <= REL
+    keep = list(range(op.real_channels))
+    for b in range(batch):
+        xs = O.slicq_slices(x[b].astype(np.float64), op)
+        for m in slices_to_check:
+            ref = np.concatenate(O.nsgt_analysis(xs[m], op.sys, keep))
+            got = c[b, m].cpu().numpy().astype(np.complex128)
+            assert _rel(got, ref) <= REL, (b, m, _rel(got, ref))
+            assert np.abs(got - ref).max() <= ELEM * np.abs(ref).max()
+
+
+def test_full_size_60s_stereo(S):
+    """60 s stereo at 44.1 kHz, B = 48, 2N = 65536, M = 16384 (the bench workload)."""
+    fs = 44100.0
+    x = signals.pink_noise_harmonic_tones(60 * 44100, fs, 2, seed=signals.seed_for(1))
+    p = S.SliCQParams(fs, 32.7, 22050.0, 48, 65536, 16384)
+    _sampled_full_size(S, p, x, [0, 1, 40, 81])
+
+
+def test_full_size_10min_48k(S):
+    """10 min mono at 48 kHz, B = 96, 2N = 131072, M = 32768 (cluster of 8)."""
+    fs = 48000.0
+    x = signals.noise_plus_chirps(600 * 48000, fs, seed=signals.seed_for(3))[None]
+    p = S.SliCQParams(fs, 27.5, 24000.0, 96, 131072, 32768)
+    _sampled_full_size(S, p, x, [0, 217, 439])
+
+
+def test_autograd_backward_is_adjoint(S):
+    """loss = sum |c|^2: torch's gradient must equal 2 Re(A^H A x) from the
+    oracle, and match an FP64 finite difference of the oracle's loss."""
+    p = S.SliCQParams(44100.0, 50.0, 22050.0, 12, 4096, 1024)
+    plan = S.SliCQPlan(p)
+    op = _oplan(p)
+    n = 9000
+    x = _signal(n, p.fs, 1, 3)[0]
+    xt = torch.from_numpy(x).cuda().requires_grad_(True)
+    c = S.slicq_transform(xt, plan)
+    loss = (c.abs() ** 2).sum()
+    loss.backward()
+    g = xt.grad.cpu().numpy()
+    x64 = x.astype(np.float64)
+    gref = 2.0 * O.slicq_adjoint(O.slicq_forward(x64, op), op, n)
+    assert _rel(g, gref) <= REL
+    v = np.random.default_rng(1).standard_normal(n)
+    h = 1e-4
+    fp = np.sum(np.abs(O.slicq_forward(x64 + h * v, op)) ** 2)
+    fm = np.sum(np.abs(O.slicq_forward(x64 - h * v, op)) ** 2)
+    fd = (fp - fm) / (2 * h)
+    assert abs(fd - float(np.dot(g, v))) <= 1e-4 * abs(fd)
