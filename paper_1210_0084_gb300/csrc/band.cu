@@ -9,37 +9,50 @@
 // slice kernel, bins beyond N are read as conjugates.
 //
 // Synthesis (Algorithm 2, loop over k and line "sum_k f_k g~_k"): Y = forward
-// DFT_{M_k}(c_k), then the half spectrum receives Y[j mod M_k] w g~_k[j] at
-// j and its conjugate at -j (when those bins lie in 0..N).  Channels are
-// accumulated in shared memory colour by colour (channels of one colour have
-// disjoint footprints), so every bin is summed in a fixed order; bins shared
-// with the neighbouring group are combined by whichever of the two CTAs
-// arrives second (a + b == b + a), so the result is deterministic and no
-// zero-fill pass is needed.
-#include <cooperative_groups.h>
-
+// DFT_{M_k}(c_k); each channel writes its weighted values Y[j mod M_k] w g~_k[j]
+// (j in J_k) to shared memory; then every half-spectrum bin h = 0..N of the
+// group sums, in a fixed order, the channels whose support covers h directly
+// and the conjugates of those covering -h.  Bins shared with the neighbouring
+// group are combined by whichever of the two CTAs arrives second
+// (a + b == b + a), so the result is deterministic and needs no zero-fill.
 #include "fft_common.cuh"
 #include "internal.h"
 
 namespace slicq {
 namespace {
 
+constexpr int kTwSmall = 1024;  // W_1024 table: twiddles of every band length
+
 struct BandArgs {
   const BandDesc* __restrict__ bands;
   const GroupDesc* __restrict__ groups;
   const BoundaryDesc* __restrict__ bounds;
   const int16_t* __restrict__ thread_band;
-  const float* __restrict__ win;   // window table of this launch
-  TwiddleTables tw;
-  float2* spec;                    // [slice][spec_stride]
-  int64_t slice_base;              // first slice of this launch
+  const float* __restrict__ win;     // window table of this launch
+  const float2* __restrict__ tw1024; // exp(-2 pi i t / 1024), t < 1024
+  float2* spec;                      // [slice][spec_stride]
+  int64_t slice_base;                // first slice of this launch
   int64_t spec_stride;
-  float2* coef;                    // [slice][cps]
+  float2* coef;                      // [slice][cps]
   int64_t cps;
-  float2* patch;                   // [slice][G-1][2][max_ovl]
-  uint32_t* cnt;                   // [slice][G-1]
+  float2* patch;                     // [slice][G-1][2][max_ovl]
+  uint32_t* cnt;                     // [slice][G-1]
   int G, max_ovl;
-  int N, log2N2;                   // N and log2(2N)
+  int N;
+};
+
+__device__ __forceinline__ void load_twiddles(const BandArgs& a, float2* s_tw) {
+  for (int i = threadIdx.x; i < kTwSmall; i += blockDim.x) s_tw[i] = __ldg(a.tw1024 + i);
+}
+
+// exp(SIGN 2 pi i x / 2^LOGM) from the shared W_1024 table
+template <int LOGM, int SIGN>
+struct BandTw {
+  const float2* s_tw;
+  __device__ __forceinline__ float2 operator()(int x) const {
+    const float2 w = s_tw[x << (10 - LOGM)];
+    return SIGN < 0 ? w : c_conj(w);
+  }
 };
 
 // ------------------------------------------------------------ analysis ---
@@ -62,11 +75,11 @@ __device__ __forceinline__ void analysis_pass1(const BandArgs& a, const BandDesc
 }
 
 template <int LOGM>
-__device__ __forceinline__ void analysis_pass2(const BandArgs& a, const BandDesc& bd, int tt,
-                                               const float2* buf, float2* __restrict__ out) {
+__device__ __forceinline__ void analysis_pass2(int tt, const float2* buf, const float2* s_tw,
+                                               float2* __restrict__ out) {
   using T = Team<LOGM>;
   float2 res[T::HELD];
-  team_pass2<LOGM, +1>(tt, buf, a.tw, a.log2N2 - LOGM, res);
+  team_pass2<LOGM, +1>(tt, buf, BandTw<LOGM, +1>{s_tw}, res);
 #pragma unroll
   for (int i = 0; i < T::J2; ++i)
 #pragma unroll
@@ -76,6 +89,7 @@ __device__ __forceinline__ void analysis_pass2(const BandArgs& a, const BandDesc
 
 __global__ void __launch_bounds__(kBandThreads) band_analysis_kernel(BandArgs a) {
   extern __shared__ float2 sm[];
+  __shared__ float2 s_tw[kTwSmall];
   const int g = blockIdx.x;
   const int64_t s = a.slice_base + blockIdx.y;
   const int t = threadIdx.x;
@@ -85,6 +99,7 @@ __global__ void __launch_bounds__(kBandThreads) band_analysis_kernel(BandArgs a)
   const int tt = t - bd.tofs;
   const float2* X = a.spec + s * a.spec_stride;
   float2* buf = sm + bd.smem_off;
+  load_twiddles(a, s_tw);
   if (k >= 0) {
     switch (bd.log2M) {
       case 4: analysis_pass1<4>(a, bd, tt, X, buf); break;
@@ -100,137 +115,193 @@ __global__ void __launch_bounds__(kBandThreads) band_analysis_kernel(BandArgs a)
   if (k >= 0) {
     float2* out = a.coef + s * a.cps + bd.coef_off;
     switch (bd.log2M) {
-      case 4: analysis_pass2<4>(a, bd, tt, buf, out); break;
-      case 5: analysis_pass2<5>(a, bd, tt, buf, out); break;
-      case 6: analysis_pass2<6>(a, bd, tt, buf, out); break;
-      case 7: analysis_pass2<7>(a, bd, tt, buf, out); break;
-      case 8: analysis_pass2<8>(a, bd, tt, buf, out); break;
-      case 9: analysis_pass2<9>(a, bd, tt, buf, out); break;
-      case 10: analysis_pass2<10>(a, bd, tt, buf, out); break;
+      case 4: analysis_pass2<4>(tt, buf, s_tw, out); break;
+      case 5: analysis_pass2<5>(tt, buf, s_tw, out); break;
+      case 6: analysis_pass2<6>(tt, buf, s_tw, out); break;
+      case 7: analysis_pass2<7>(tt, buf, s_tw, out); break;
+      case 8: analysis_pass2<8>(tt, buf, s_tw, out); break;
+      case 9: analysis_pass2<9>(tt, buf, s_tw, out); break;
+      case 10: analysis_pass2<10>(tt, buf, s_tw, out); break;
     }
   }
 }
 
 // ----------------------------------------------------------- synthesis ---
 
-// Barrier that threads may reach from different code locations (the band
-// pipelines below are different template instances per band length; every
-// thread of the CTA executes the same number of these barriers).
-__device__ __forceinline__ void cta_sync() { asm volatile("barrier.sync 0;" ::: "memory"); }
+// Per-channel fields the gather needs, staged in shared memory.
+struct GatherBand {
+  int32_t dlo, dhi;   // direct bins [dlo, dhi] (dhi < 0: none)
+  int32_t j0, base;   // support start on the circle, contribution offset in smem
+};
 
-// MIRROR = false: Y w g~ into bin j (if j <= N); true: its conjugate into -j.
-template <int LOGM, bool MIRROR>
-__device__ __forceinline__ void synthesis_accumulate(const BandArgs& a, const BandDesc& bd, int tt,
-                                                     const float2* res, float2* acc, int acc_lo) {
+template <int LOGM>
+__device__ __forceinline__ void synthesis_pass1(int tt, const float2* __restrict__ c, float2* buf) {
+  team_pass1<LOGM, -1>(tt, buf, [&](int idx) { return __ldcs(c + idx); });
+}
+
+template <int LOGM>
+__device__ __forceinline__ void synthesis_pass2(int tt, const float2* s_tw, const float2* buf,
+                                                float2* res) {
+  team_pass2<LOGM, -1>(tt, buf, BandTw<LOGM, -1>{s_tw}, res);
+}
+
+// Weighted values Y[j mod M] w g~[j] stored at their support offsets o = j - j0.
+template <int LOGM>
+__device__ __forceinline__ void synthesis_weight(const BandArgs& a, const BandDesc& bd, int tt,
+                                                 const float2* res, float2* contrib) {
   using T = Team<LOGM>;
   constexpr int M = 1 << LOGM;
-  const int twoN = 2 * a.N;
   const float* __restrict__ g = a.win + bd.win_off;
 #pragma unroll
-  for (int i = 0; i < T::J2; ++i) {
+  for (int i = 0; i < T::J2; ++i)
 #pragma unroll
     for (int r = 0; r < T::R2; ++r) {
       const int idx = team_out_index<LOGM>(tt, i, r);
       const int o = (idx - bd.j0) & (M - 1);
-      if (o < bd.len) {
-        int b = bd.j0 + o;
-        if (b >= twoN) b -= twoN;
-        const float2 v = c_scale(res[i * T::R2 + r], __ldg(g + o));
-        if (!MIRROR) {
-          if (b <= a.N) acc[b - acc_lo] = c_add(acc[b - acc_lo], v);
-        } else {
-          const int mb = b == 0 ? 0 : twoN - b;
-          if (mb <= a.N) acc[mb - acc_lo] = c_add(acc[mb - acc_lo], c_conj(v));
-        }
-      }
+      if (o < bd.len) contrib[o] = c_scale(res[i * T::R2 + r], __ldg(g + o));
     }
-  }
 }
 
-// Hand a shared boundary to the neighbour or, if the neighbour already
-// handed over its half, add both halves and store them.  side 0 = this
-// group is left of the boundary.  No waiting: the first arriver leaves.
-__device__ __forceinline__ void boundary_combine(const BandArgs& a, int64_t s, int bd, int side,
-                                                 const float2* acc, int acc_lo, float2* spec,
-                                                 int* s_flag) {
-  const BoundaryDesc b = a.bounds[bd];
-  const int64_t slot = s * (a.G - 1) + bd;
-  float2* mine = a.patch + (slot * 2 + side) * a.max_ovl;
-  const float2* other = a.patch + (slot * 2 + (1 - side)) * a.max_ovl;
-  for (int h = b.lo + threadIdx.x; h < b.hi; h += blockDim.x) mine[h - b.lo] = acc[h - acc_lo];
-  __threadfence();
-  cta_sync();
-  if (threadIdx.x == 0) {
-    // 0 -> 1 for the first arriver, 1 -> 0 for the second (ready for the next call)
-    const unsigned old = atomicInc(a.cnt + slot, 1u);
-    *s_flag = (old == 1u);
+// Sum of all contributions to half-spectrum bin h, in a fixed order: direct
+// channels from the highest covering one down, then the mirrored channels.
+__device__ __forceinline__ float2 gather_bin(int h, int& last, int nb, const GatherBand* gb,
+                                             const GroupDesc& gd, const BandDesc* __restrict__ bands,
+                                             const float2* sm, int twoN) {
+  while (last + 1 < nb && gb[last + 1].dlo <= h) ++last;
+  float2 acc = make_float2(0.f, 0.f);
+  for (int k = last; k >= 0; --k) {
+    const GatherBand b = gb[k];
+    if (b.dhi < 0) continue;          // channel without support
+    if (b.dhi < h) break;             // dhi is non-decreasing over the group
+    int o = h - b.j0;
+    if (o < 0) o += twoN;
+    acc = c_add(acc, sm[b.base + o]);
   }
-  cta_sync();
-  if (*s_flag) {
-    __threadfence();
-    for (int h = b.lo + threadIdx.x; h < b.hi; h += blockDim.x)
-      spec[h] = c_add(acc[h - acc_lo], __ldcg(other + (h - b.lo)));
+  for (int i = 0; i < gd.nmirror; ++i) {
+    const BandDesc bd = bands[gd.mirror[i]];
+    if (h < bd.mlo || h > bd.mhi) continue;
+    const int bm = h == 0 ? 0 : twoN - h;
+    int o = bm - bd.j0;
+    if (o < 0) o += twoN;
+    if (o < bd.len) acc = c_add(acc, c_conj(sm[bd.smem_off + o]));
   }
-  cta_sync();
-}
-
-// The whole synthesis pipeline of one CTA as seen by one thread.  LOGM = 0
-// is a thread without a band: it only takes part in the barriers and the
-// CTA-wide loops.
-template <int LOGM>
-__device__ __forceinline__ void synthesis_pipeline(const BandArgs& a, const GroupDesc& gd,
-                                                   const BandDesc& bd, int tt, int64_t s,
-                                                   float2* sm, int* s_flag) {
-  constexpr int LG = LOGM ? LOGM : 4;
-  using T = Team<LG>;
-  float2 res[T::HELD];
-  float2* buf = sm + bd.smem_off;
-  if (LOGM) {
-    const float2* c = a.coef + s * a.cps + bd.coef_off;
-    team_pass1<LG, -1>(tt, buf, [&](int idx) { return __ldcs(c + idx); });
-  }
-  cta_sync();
-  if (LOGM) team_pass2<LG, -1>(tt, buf, a.tw, a.log2N2 - LG, res);
-  cta_sync();
-  // the whole shared buffer becomes the accumulator of bins [acc_lo, acc_hi)
-  float2* acc = sm;
-  const int nacc = gd.acc_hi - gd.acc_lo;
-  for (int h = threadIdx.x; h < nacc; h += blockDim.x) acc[h] = make_float2(0.f, 0.f);
-  cta_sync();
-  for (int col = 0; col < gd.ncolor; ++col) {
-    if (LOGM && bd.color == col) synthesis_accumulate<LG, false>(a, bd, tt, res, acc, gd.acc_lo);
-    cta_sync();
-    if (gd.any_mirror) {
-      if (LOGM && bd.color == col && bd.mirror) synthesis_accumulate<LG, true>(a, bd, tt, res, acc, gd.acc_lo);
-      cta_sync();
-    }
-  }
-  float2* spec = a.spec + s * a.spec_stride;
-  for (int h = gd.ex_lo + threadIdx.x; h < gd.ex_hi; h += blockDim.x) spec[h] = acc[h - gd.acc_lo];
-  if (gd.left_bd >= 0) boundary_combine(a, s, gd.left_bd, 1, acc, gd.acc_lo, spec, s_flag);
-  if (gd.right_bd >= 0) boundary_combine(a, s, gd.right_bd, 0, acc, gd.acc_lo, spec, s_flag);
+  return acc;
 }
 
 __global__ void __launch_bounds__(kBandThreads) band_synthesis_kernel(BandArgs a) {
   extern __shared__ float2 sm[];
+  __shared__ float2 s_tw[kTwSmall];
+  __shared__ GatherBand s_gb[kBandThreads];
   __shared__ int s_flag;
   const int g = blockIdx.x;
   const int64_t s = a.slice_base + blockIdx.y;
   const int t = threadIdx.x;
   const int k = a.thread_band[g * kBandThreads + t];
   const GroupDesc gd = a.groups[g];
+  const int nb = gd.band_end - gd.band_begin;
   BandDesc bd{};
   if (k >= 0) bd = a.bands[k];
   const int tt = t - bd.tofs;
-  switch (k >= 0 ? bd.log2M : 0) {
-    case 4: synthesis_pipeline<4>(a, gd, bd, tt, s, sm, &s_flag); break;
-    case 5: synthesis_pipeline<5>(a, gd, bd, tt, s, sm, &s_flag); break;
-    case 6: synthesis_pipeline<6>(a, gd, bd, tt, s, sm, &s_flag); break;
-    case 7: synthesis_pipeline<7>(a, gd, bd, tt, s, sm, &s_flag); break;
-    case 8: synthesis_pipeline<8>(a, gd, bd, tt, s, sm, &s_flag); break;
-    case 9: synthesis_pipeline<9>(a, gd, bd, tt, s, sm, &s_flag); break;
-    case 10: synthesis_pipeline<10>(a, gd, bd, tt, s, sm, &s_flag); break;
-    default: synthesis_pipeline<0>(a, gd, bd, tt, s, sm, &s_flag); break;
+  float2* buf = sm + bd.smem_off;
+  const int twoN = 2 * a.N;
+
+  load_twiddles(a, s_tw);
+  if (t < nb) {
+    const BandDesc b = a.bands[gd.band_begin + t];
+    s_gb[t] = GatherBand{b.dlo, b.dhi, b.j0, b.smem_off};
+  }
+  if (k >= 0) {
+    const float2* c = a.coef + s * a.cps + bd.coef_off;
+    switch (bd.log2M) {
+      case 4: synthesis_pass1<4>(tt, c, buf); break;
+      case 5: synthesis_pass1<5>(tt, c, buf); break;
+      case 6: synthesis_pass1<6>(tt, c, buf); break;
+      case 7: synthesis_pass1<7>(tt, c, buf); break;
+      case 8: synthesis_pass1<8>(tt, c, buf); break;
+      case 9: synthesis_pass1<9>(tt, c, buf); break;
+      case 10: synthesis_pass1<10>(tt, c, buf); break;
+    }
+  }
+  __syncthreads();
+  float2 res[kPerThread];
+  if (k >= 0) {
+    switch (bd.log2M) {
+      case 4: synthesis_pass2<4>(tt, s_tw, buf, res); break;
+      case 5: synthesis_pass2<5>(tt, s_tw, buf, res); break;
+      case 6: synthesis_pass2<6>(tt, s_tw, buf, res); break;
+      case 7: synthesis_pass2<7>(tt, s_tw, buf, res); break;
+      case 8: synthesis_pass2<8>(tt, s_tw, buf, res); break;
+      case 9: synthesis_pass2<9>(tt, s_tw, buf, res); break;
+      case 10: synthesis_pass2<10>(tt, s_tw, buf, res); break;
+    }
+  }
+  __syncthreads();  // every team has read its pass buffer: reuse it for contributions
+  if (k >= 0) {
+    switch (bd.log2M) {
+      case 4: synthesis_weight<4>(a, bd, tt, res, buf); break;
+      case 5: synthesis_weight<5>(a, bd, tt, res, buf); break;
+      case 6: synthesis_weight<6>(a, bd, tt, res, buf); break;
+      case 7: synthesis_weight<7>(a, bd, tt, res, buf); break;
+      case 8: synthesis_weight<8>(a, bd, tt, res, buf); break;
+      case 9: synthesis_weight<9>(a, bd, tt, res, buf); break;
+      case 10: synthesis_weight<10>(a, bd, tt, res, buf); break;
+    }
+  }
+  __syncthreads();
+
+  // gather bins [acc_lo, acc_hi); bins shared with a neighbour go to hand-off slots
+  float2* spec = a.spec + s * a.spec_stride;
+  int bl_hi = gd.acc_lo, br_lo = gd.acc_hi;
+  float2* patch_l = nullptr;
+  float2* patch_r = nullptr;
+  if (gd.left_bd >= 0) {
+    bl_hi = a.bounds[gd.left_bd].hi;
+    patch_l = a.patch + ((s * (a.G - 1) + gd.left_bd) * 2 + 1) * a.max_ovl - gd.acc_lo;
+  }
+  if (gd.right_bd >= 0) {
+    br_lo = a.bounds[gd.right_bd].lo;
+    patch_r = a.patch + ((s * (a.G - 1) + gd.right_bd) * 2 + 0) * a.max_ovl - br_lo;
+  }
+  {
+    int h = gd.acc_lo + t;
+    int last = -1;
+    if (h < gd.acc_hi) {  // last channel with dlo <= h (dlo is non-decreasing)
+      int lo = 0, hi = nb - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (s_gb[mid].dlo <= h) lo = mid; else hi = mid - 1;
+      }
+      last = s_gb[lo].dlo <= h ? lo : -1;
+    }
+    for (; h < gd.acc_hi; h += blockDim.x) {
+      const float2 v = gather_bin(h, last, nb, s_gb, gd, a.bands, sm, twoN);
+      if (h < bl_hi) patch_l[h] = v;
+      else if (h >= br_lo) patch_r[h] = v;
+      else spec[h] = v;
+    }
+  }
+  // hand-offs: the second CTA to arrive at a shared range stores the sums
+#pragma unroll 1
+  for (int side = 0; side < 2; ++side) {
+    const int bd_i = side == 0 ? gd.left_bd : gd.right_bd;
+    if (bd_i < 0) continue;
+    const BoundaryDesc b = a.bounds[bd_i];
+    const int64_t slot = s * (a.G - 1) + bd_i;
+    __threadfence();
+    __syncthreads();
+    if (t == 0) {
+      // 0 -> 1 for the first arriver, 1 -> 0 for the second (ready for the next call)
+      const unsigned old = atomicInc(a.cnt + slot, 1u);
+      s_flag = (old == 1u);
+    }
+    __syncthreads();
+    if (s_flag) {
+      __threadfence();
+      const float2* p0 = a.patch + (slot * 2 + 0) * a.max_ovl;
+      const float2* p1 = a.patch + (slot * 2 + 1) * a.max_ovl;
+      for (int h = b.lo + t; h < b.hi; h += blockDim.x)
+        spec[h] = c_add(__ldcg(p0 + (h - b.lo)), __ldcg(p1 + (h - b.lo)));
+    }
   }
 }
 
@@ -241,7 +312,7 @@ BandArgs make_args(const slicq_plan* pl, const Workspace& ws, const float* win) 
   a.bounds = pl->d_bounds;
   a.thread_band = pl->d_thread_band;
   a.win = win;
-  a.tw = TwiddleTables{pl->d_tw_lo, pl->d_tw_hi, pl->tw_lb};
+  a.tw1024 = pl->d_tw1024;
   a.spec = ws.spec;
   a.spec_stride = ws.spec_stride;
   a.cps = pl->coefs_per_slice;
@@ -250,7 +321,6 @@ BandArgs make_args(const slicq_plan* pl, const Workspace& ws, const float* win) 
   a.G = pl->G;
   a.max_ovl = pl->max_ovl;
   a.N = (int)pl->N;
-  a.log2N2 = ilog2c((int)(2 * pl->N));
   return a;
 }
 

@@ -158,10 +158,9 @@ __device__ __forceinline__ void team_pass1(int tt, float2* __restrict__ buf, Loa
 }
 
 // Pass 2 (read half): twiddled, transformed values into res[i * R2 + r] for
-// element (tt + TT i) + r R1.  tw_shift = log2(2N / Lf).
-template <int LOGL, int SIGN>
-__device__ __forceinline__ void team_pass2(int tt, const float2* __restrict__ buf,
-                                           const TwiddleTables& tw, int tw_shift,
+// element (tt + TT i) + r R1.  TW(x) returns exp(SIGN 2 pi i x / Lf).
+template <int LOGL, int SIGN, class Tw>
+__device__ __forceinline__ void team_pass2(int tt, const float2* __restrict__ buf, Tw tw,
                                            float2* __restrict__ res) {
   using T = Team<LOGL>;
 #pragma unroll
@@ -171,7 +170,7 @@ __device__ __forceinline__ void team_pass2(int tt, const float2* __restrict__ bu
 #pragma unroll
     for (int r = 0; r < T::R2; ++r) {
       float2 x = buf[T::pad2(j, r)];
-      if (r > 0) x = c_mul(x, twiddle_s<SIGN>(tw, (uint32_t)(j * r) << tw_shift));
+      if (r > 0) x = c_mul(x, tw(j * r));
       v[r] = x;
     }
     dft_reg<T::R2, SIGN>(v);
@@ -179,6 +178,16 @@ __device__ __forceinline__ void team_pass2(int tt, const float2* __restrict__ bu
     for (int r = 0; r < T::R2; ++r) res[i * T::R2 + r] = v[r];
   }
 }
+
+// Shared-memory copy of the two-level table exp(-2 pi i t / 2N).
+struct SmemTwiddles {
+  const float2* lo;
+  const float2* hi;
+  int lb;
+  __device__ __forceinline__ float2 operator()(uint32_t t) const {
+    return c_mul(lo[t & ((1u << lb) - 1u)], hi[t >> lb]);
+  }
+};
 
 // Element index of res[i * R2 + r] after team_pass2.
 template <int LOGL>

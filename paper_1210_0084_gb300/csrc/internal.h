@@ -28,8 +28,8 @@ struct BandDesc {
   int32_t win_off;   // offset into the window tables
   int32_t tofs;      // first thread of the band's team inside the group CTA
   int32_t smem_off;  // complex offset of the team's buffer in shared memory
-  int32_t color;     // accumulation colour (disjoint footprints per colour)
-  int32_t mirror;    // 1 if some support bin maps to the half spectrum mirrored
+  int32_t dlo, dhi;  // half-spectrum bins the support covers directly (dhi < 0: none)
+  int32_t mlo, mhi;  // half-spectrum bins -j for j in the support (mlo > mhi: none)
   int32_t pad_;
 };
 
@@ -38,9 +38,9 @@ struct GroupDesc {
   int32_t band_begin, band_end;  // channels [begin, end)
   int32_t acc_lo, acc_hi;        // half-spectrum bins the group touches
   int32_t ex_lo, ex_hi;          // bins only this group touches
-  int32_t ncolor;                // colour classes
-  int32_t any_mirror;            // some band has mirrored bins
   int32_t left_bd, right_bd;     // boundary indices, -1 if none
+  int32_t nmirror;               // channels of the group with mirrored bins
+  int32_t mirror[16];            // their indices
 };
 
 // Bins [lo, hi) touched by two neighbouring groups (bd and bd + 1).
@@ -66,6 +66,7 @@ struct slicq_plan {
   int max_ovl = 0;        // longest group-boundary overlap (bins)
   int band_smem = 0;      // dynamic shared memory of the band kernels (bytes)
   int slice_smem = 0;     // dynamic shared memory of the slice kernels (bytes)
+  int slice_tw_off = 0;   // float2 offset of the twiddle tables in that memory
   int tw_lb = 0;          // log2 of the fine twiddle table length
   int64_t win_total = 0;  // sum_k |J_k|
 
@@ -88,6 +89,7 @@ struct slicq_plan {
   float* d_hw = nullptr;    // Tukey transition, M + 1 values
   float2* d_tw_lo = nullptr;  // exp(-2 pi i t / 2N), t < 2^tw_lb
   float2* d_tw_hi = nullptr;  // exp(-2 pi i (t << tw_lb) / 2N)
+  float2* d_tw1024 = nullptr; // exp(-2 pi i t / 1024), t < 1024
 
   // optional kernel timing trace (events around every launch)
   struct Trace {

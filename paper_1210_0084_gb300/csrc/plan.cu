@@ -109,20 +109,30 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
     pl->jlo[k] = first;
     coef_off += M;
     win_off += count;
-    // footprint in the half spectrum 0..N and mirror flag
-    int flo = (int)N + 1, fhi = -1, mirror = 0;
+    // half-spectrum footprint: direct bins b <= N, mirrored bins 2N - b for b >= N or b = 0
+    int dlo = (int)N + 1, dhi = -1, mlo = (int)N + 1, mhi = -1;
     for (int64_t o = 0; o < count; ++o) {
       const int64_t b = (bd.j0 + o) % L2;
-      const int64_t h = b <= N ? b : L2 - b;
-      if (b == 0 || b == N || b > N) mirror = 1;
-      flo = std::min<int>(flo, (int)h);
-      fhi = std::max<int>(fhi, (int)h);
-      cover[h] += 1;
+      if (b <= N) {
+        if (dhi >= 0 && b != dhi + 1) return SLICQ_EUNSUPPORTED;  // direct part must be an interval
+        dlo = std::min<int>(dlo, (int)b);
+        dhi = (int)b;
+        cover[b] += 1;
+      }
+      if (b == 0 || b >= N) {
+        const int64_t h = (L2 - b) % L2;
+        mlo = std::min<int>(mlo, (int)h);
+        mhi = std::max<int>(mhi, (int)h);
+        cover[h] += 1;
+      }
     }
-    if (count == 0) { flo = fhi = (int)std::min<int64_t>(std::max<int64_t>(bd.j0 <= N ? bd.j0 : L2 - bd.j0, 0), N); }
-    bd.mirror = mirror;
-    foot_lo[k] = flo;
-    foot_hi[k] = fhi;
+    bd.dlo = dlo;
+    bd.dhi = dhi;
+    bd.mlo = mlo;
+    bd.mhi = mhi;
+    foot_lo[k] = std::min(dhi >= 0 ? dlo : (int)N + 1, mhi >= 0 ? mlo : (int)N + 1);
+    foot_hi[k] = std::max(dhi, mhi);
+    if (count == 0) foot_lo[k] = foot_hi[k] = -1;
   }
   for (int64_t h = 0; h <= N; ++h)
     if (cover[h] == 0) return SLICQ_EINVAL;  // eq. painlessframe1 fails: d[h] = 0
@@ -154,25 +164,30 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
       }
       gd.band_end = k;
       int alo = (int)N + 1, ahi = -1;
-      gd.any_mirror = 0;
+      gd.nmirror = 0;
+      int prev_dlo = 0, prev_dhi = -1;
       for (int b = gd.band_begin; b < gd.band_end; ++b) {
-        alo = std::min(alo, foot_lo[b]);
-        ahi = std::max(ahi, foot_hi[b]);
-        gd.any_mirror |= pl->bands[b].mirror;
+        BandDesc& d = pl->bands[b];
+        if (foot_hi[b] >= 0) {
+          alo = std::min(alo, foot_lo[b]);
+          ahi = std::max(ahi, foot_hi[b]);
+        }
+        if (d.dhi < 0) {  // no direct bins: keep dlo monotone, mark empty
+          d.dlo = prev_dlo;
+        } else {
+          if (d.dlo < prev_dlo || d.dhi < prev_dhi) return SLICQ_EUNSUPPORTED;
+          prev_dlo = d.dlo;
+          prev_dhi = d.dhi;
+        }
+        if (d.mhi >= 0) {
+          if (gd.nmirror == 16) return SLICQ_EUNSUPPORTED;
+          gd.mirror[gd.nmirror++] = b;
+        }
       }
+      if (ahi < 0) return SLICQ_EINVAL;
       gd.acc_lo = alo;
       gd.acc_hi = ahi + 1;
-      band_smem_c = std::max(band_smem_c, std::max(smem, gd.acc_hi - gd.acc_lo));
-      // greedy interval colouring of the footprints (in channel order)
-      std::vector<int> col_end;
-      for (int b = gd.band_begin; b < gd.band_end; ++b) {
-        int c = 0;
-        while (c < (int)col_end.size() && col_end[c] >= foot_lo[b]) ++c;
-        if (c == (int)col_end.size()) col_end.push_back(-1);
-        col_end[c] = std::max(col_end[c], foot_hi[b]);
-        pl->bands[b].color = c;
-      }
-      gd.ncolor = (int)col_end.size();
+      band_smem_c = std::max(band_smem_c, smem);
       pl->groups.push_back(gd);
       std::vector<int16_t> tb(kBandThreads, (int16_t)-1);
       for (int b = gd.band_begin; b < gd.band_end; ++b) {
@@ -240,9 +255,11 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
     const int xs1 = (Qn / C) * (P + 1);
     const int cs3 = (P / C) * (Qn + R2q + 1);
     const int zs3 = (P / C) * (Qn + 1);
-    pl->slice_smem = std::max(std::max(cs1, xs1), std::max(cs3, zs3)) * (int)sizeof(float2);
+    pl->tw_lb = (ilog2_64(L2) + 1) / 2;
+    pl->slice_tw_off = std::max(std::max(cs1, xs1), std::max(cs3, zs3));
+    const int ntw = (1 << pl->tw_lb) + (int)(L2 >> pl->tw_lb);
+    pl->slice_smem = (pl->slice_tw_off + ntw) * (int)sizeof(float2);
   }
-  pl->tw_lb = (ilog2_64(L2) + 1) / 2;
   return SLICQ_OK;
 }
 
@@ -326,9 +343,15 @@ __global__ void k_duals(const WinJob* jobs, int nch, int64_t total, const double
   gadj[i] = (float)(0.5 * g * s);
 }
 
-// exp(-2 pi i t / L2): fine table t < 2^lb, coarse table (t << lb)
-__global__ void k_twiddles(int64_t L2, int lb, float2* lo, float2* hi) {
+// exp(-2 pi i t / L2): fine table t < 2^lb, coarse table (t << lb); and
+// exp(-2 pi i t / 1024) for the band transforms
+__global__ void k_twiddles(int64_t L2, int lb, float2* lo, float2* hi, float2* t1024) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < 1024) {
+    double s, c;
+    sincospi(-2.0 * (double)i / 1024.0, &s, &c);
+    t1024[i] = make_float2((float)c, (float)s);
+  }
   const int64_t nlo = int64_t(1) << lb;
   const int64_t nhi = L2 >> lb;
   if (i < nlo) {
@@ -372,6 +395,7 @@ slicq_status build_tables(slicq_plan* pl) {
   const size_t o_hw = take(sizeof(float) * (Mtr + 1));
   const size_t o_twlo = take(sizeof(float2) * (size_t(1) << pl->tw_lb));
   const size_t o_twhi = take(sizeof(float2) * (L2 >> pl->tw_lb));
+  const size_t o_tw1024 = take(sizeof(float2) * 1024);
   if (cudaMalloc(&pl->d_arena, off) != cudaSuccess) return SLICQ_ENOMEM;
   char* base = (char*)pl->d_arena;
   pl->d_bands = (BandDesc*)(base + o_bands);
@@ -384,6 +408,7 @@ slicq_status build_tables(slicq_plan* pl) {
   pl->d_hw = (float*)(base + o_hw);
   pl->d_tw_lo = (float2*)(base + o_twlo);
   pl->d_tw_hi = (float2*)(base + o_twhi);
+  pl->d_tw1024 = (float2*)(base + o_tw1024);
 
   slicq_status st = SLICQ_OK;
   cudaError_t e = cudaSuccess;
@@ -437,8 +462,9 @@ slicq_status build_tables(slicq_plan* pl) {
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-      const int64_t nt = std::max<int64_t>(int64_t(1) << pl->tw_lb, L2 >> pl->tw_lb);
-      k_twiddles<<<(unsigned)((nt + T - 1) / T), T>>>(L2, pl->tw_lb, pl->d_tw_lo, pl->d_tw_hi);
+      const int64_t nt = std::max<int64_t>(std::max<int64_t>(int64_t(1) << pl->tw_lb, L2 >> pl->tw_lb), 1024);
+      k_twiddles<<<(unsigned)((nt + T - 1) / T), T>>>(L2, pl->tw_lb, pl->d_tw_lo, pl->d_tw_hi,
+                                                      pl->d_tw1024);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) {

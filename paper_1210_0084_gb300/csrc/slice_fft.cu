@@ -39,7 +39,8 @@ struct SliceArgs {
   int S, N, Mtr;
   int C, logQc, logPc;
   const float* __restrict__ hw;   // Tukey transition, Mtr + 1 values
-  TwiddleTables tw;
+  TwiddleTables tw;               // global two-level tables (copied to shared memory)
+  int tw_off;                     // shared-memory offset (float2) of the table copy
   float* ola_patch;               // [slice][2][Mtr]
   uint32_t* ola_cnt;              // [slice][C]
   int adjoint;                    // multiply the output by h_0 instead of 1
@@ -69,10 +70,31 @@ struct Geo {
 // returns input element e (0 <= e < N).  On return res[i * R2q + r] holds
 // Z[u + P v] for u = rank * P/C + ul, v = (tt + TTq i) + r R1q, and the shared
 // memory may be reused after a __syncthreads().
+template <int SIGN>
+struct SliceTw {  // exp(SIGN 2 pi i x / 2^(log2N2 - shift)) from the shared tables
+  SmemTwiddles t;
+  int shift;
+  __device__ __forceinline__ float2 operator()(int x) const {
+    const float2 w = t((uint32_t)x << shift);
+    return SIGN < 0 ? w : c_conj(w);
+  }
+};
+
+// Copy the two-level twiddle tables to shared memory (caller synchronises).
+__device__ __forceinline__ SmemTwiddles stage_twiddles(const SliceArgs& a, float2* sm) {
+  float2* lo = sm + a.tw_off;
+  const int nlo = 1 << a.tw.lb;
+  float2* hi = lo + nlo;
+  const int nhi = (2 * a.N) >> a.tw.lb;
+  for (int i = threadIdx.x; i < nlo; i += blockDim.x) lo[i] = __ldg(a.tw.lo + i);
+  for (int i = threadIdx.x; i < nhi; i += blockDim.x) hi[i] = __ldg(a.tw.hi + i);
+  return SmemTwiddles{lo, hi, a.tw.lb};
+}
+
 template <int LOGP, int LOGQ, int SIGN, class Load>
 __device__ __forceinline__ void fourstep(const SliceArgs& a, cg::cluster_group& cluster,
-                                         float2* sm, Load load, float2* res, int& ul_out,
-                                         int& tt_out) {
+                                         float2* sm, const SmemTwiddles& tws, Load load,
+                                         float2* res, int& ul_out, int& tt_out) {
   using G = Geo<LOGP, LOGQ>;
   using TP = typename G::TP;
   using TQ = typename G::TQ;
@@ -90,7 +112,7 @@ __device__ __forceinline__ void fourstep(const SliceArgs& a, cg::cluster_group& 
     team_pass1<LOGP, SIGN>(tt, buf, [&](int p) { return load(p * G::Q + q); });
     __syncthreads();
     float2 col[TP::HELD];
-    team_pass2<LOGP, SIGN>(tt, buf, a.tw, log2N2 - LOGP, col);
+    team_pass2<LOGP, SIGN>(tt, buf, SliceTw<SIGN>{tws, log2N2 - LOGP}, col);
     __syncthreads();
     // four-step twiddle W_N^{q u} = W_2N^{2 q u}, then the exchange layout [ql][u]
 #pragma unroll
@@ -100,7 +122,7 @@ __device__ __forceinline__ void fourstep(const SliceArgs& a, cg::cluster_group& 
         const int u = team_out_index<LOGP>(tt, i, r);
         float2 v = col[i * TP::R2 + r];
         const uint32_t e = ((uint32_t)(q * u) & ((1u << (LOGP + LOGQ)) - 1u)) << 1;
-        if (e) v = c_mul(v, twiddle_s<SIGN>(a.tw, e));
+        if (e) v = c_mul(v, SliceTw<SIGN>{tws, 0}((int)e));
         sm[ql * G::XS1 + u] = v;
       }
   }
@@ -138,7 +160,7 @@ __device__ __forceinline__ void fourstep(const SliceArgs& a, cg::cluster_group& 
       for (int r = 0; r < TQ::R1; ++r) buf[TQ::pad1(j, r)] = v[r];
     }
     __syncthreads();
-    team_pass2<LOGQ, SIGN>(tt, buf, a.tw, log2N2 - LOGQ, res);
+    team_pass2<LOGQ, SIGN>(tt, buf, SliceTw<SIGN>{tws, log2N2 - LOGQ}, res);
   }
   ul_out = ul;
   tt_out = tt;
@@ -147,7 +169,7 @@ __device__ __forceinline__ void fourstep(const SliceArgs& a, cg::cluster_group& 
 // ------------------------------------------------------------- forward ---
 
 template <int LOGP, int LOGQ>
-__global__ void __launch_bounds__(kSliceMaxThreads) slice_forward_kernel(SliceArgs a) {
+__global__ void __launch_bounds__(kSliceMaxThreads, 2) slice_forward_kernel(SliceArgs a) {
   using G = Geo<LOGP, LOGQ>;
   using TQ = typename G::TQ;
   extern __shared__ float2 sm[];
@@ -168,40 +190,45 @@ __global__ void __launch_bounds__(kSliceMaxThreads) slice_forward_kernel(SliceAr
   };
   auto load = [&](int e) -> float2 { return make_float2(sample(2 * e), sample(2 * e + 1)); };
 
-  float2 res[TQ::HELD];
-  int ul, tt;
-  fourstep<LOGP, LOGQ, -1>(a, cluster, sm, load, res, ul, tt);
+  const SmemTwiddles tws = stage_twiddles(a, sm);
   __syncthreads();
-  // Z rows to shared memory for the even/odd split (needs Z[N - k])
+  {
+    float2 res[TQ::HELD];
+    int ul, tt;
+    fourstep<LOGP, LOGQ, -1>(a, cluster, sm, tws, load, res, ul, tt);
+    __syncthreads();
+    // Z rows to shared memory for the even/odd split (needs Z[N - k])
 #pragma unroll
-  for (int i = 0; i < TQ::J2; ++i)
+    for (int i = 0; i < TQ::J2; ++i)
 #pragma unroll
-    for (int r = 0; r < TQ::R2; ++r) sm[ul * G::ZS3 + team_out_index<LOGQ>(tt, i, r)] = res[i * TQ::R2 + r];
+      for (int r = 0; r < TQ::R2; ++r)
+        sm[ul * G::ZS3 + team_out_index<LOGQ>(tt, i, r)] = res[i * TQ::R2 + r];
+  }
   cluster.sync();
 
+  // X[k], k = u + P v for this CTA's rows u; X[N] from k = 0
   const int Pc = 1 << a.logPc;
   const int rank = (int)cluster.block_rank();
-  const int u = rank * Pc + ul;
   float2* X = a.spec + s * a.spec_stride;
-#pragma unroll
-  for (int i = 0; i < TQ::J2; ++i)
-#pragma unroll
-    for (int r = 0; r < TQ::R2; ++r) {
-      const int v = team_out_index<LOGQ>(tt, i, r);
-      const int k = u + G::P * v;
-      int up, vp;
-      if (u == 0) { up = 0; vp = (G::Q - v) & (G::Q - 1); }
-      else { up = G::P - u; vp = G::Q - 1 - v; }
-      const float2* rsm = cluster.map_shared_rank(sm, up >> a.logPc);
-      const float2 zp = c_conj(rsm[(up & (Pc - 1)) * G::ZS3 + vp]);
-      const float2 z = res[i * TQ::R2 + r];
-      // even part E = (Z[k] + conj Z[N-k]) / 2, odd part O = (Z[k] - conj Z[N-k]) / 2i
-      const float2 E = c_scale(c_add(z, zp), 0.5f);
-      const float2 D = c_sub(z, zp);
-      const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);
-      X[k] = c_add(E, c_mul(twiddle(a.tw, (uint32_t)k), O));
-      if (k == 0) X[a.N] = c_sub(E, O);
-    }
+  const int held = Pc * G::Q;
+  for (int idx = threadIdx.x; idx < held; idx += blockDim.x) {
+    const int ul = idx & (Pc - 1);
+    const int v = idx >> a.logPc;
+    const int u = rank * Pc + ul;
+    const int k = u + G::P * v;
+    int up, vp;
+    if (u == 0) { up = 0; vp = (G::Q - v) & (G::Q - 1); }
+    else { up = G::P - u; vp = G::Q - 1 - v; }
+    const float2* rsm = cluster.map_shared_rank(sm, up >> a.logPc);
+    const float2 zp = c_conj(rsm[(up & (Pc - 1)) * G::ZS3 + vp]);
+    const float2 z = sm[ul * G::ZS3 + v];
+    // even part E = (Z[k] + conj Z[N-k]) / 2, odd part O = (Z[k] - conj Z[N-k]) / 2i
+    const float2 E = c_scale(c_add(z, zp), 0.5f);
+    const float2 D = c_sub(z, zp);
+    const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);
+    X[k] = c_add(E, c_mul(tws((uint32_t)k), O));
+    if (k == 0) X[a.N] = c_sub(E, O);
+  }
   cluster.sync();  // keep this CTA's shared memory alive for its neighbours
 }
 
@@ -245,19 +272,21 @@ __global__ void __launch_bounds__(kSliceMaxThreads) slice_inverse_kernel(SliceAr
   const float2* H = a.spec + s * a.spec_stride;
   const int N = a.N;
 
+  const SmemTwiddles tws = stage_twiddles(a, sm);
+  __syncthreads();
   // Z[k] = (H[k] + conj H[N-k]) + i e^{+2 pi i k / 2N} (H[k] - conj H[N-k])
   auto load = [&](int k) -> float2 {
     const float2 h = H[k];
     const float2 hc = c_conj(H[N - k]);
     const float2 sum = c_add(h, hc);
-    const float2 dif = c_mul(c_sub(h, hc), twiddle_s<+1>(a.tw, (uint32_t)k));
+    const float2 dif = c_mul(c_sub(h, hc), c_conj(tws((uint32_t)k)));
     return make_float2(sum.x - dif.y, sum.y + dif.x);
   };
 
   {
     float2 res[TQ::HELD];
     int ul, tt;
-    fourstep<LOGP, LOGQ, +1>(a, cluster, sm, load, res, ul, tt);
+    fourstep<LOGP, LOGQ, +1>(a, cluster, sm, tws, load, res, ul, tt);
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < TQ::J2; ++i)
@@ -377,6 +406,7 @@ SliceArgs make_args(const slicq_plan* pl, const Workspace& ws, int64_t n) {
   a.logPc = pl->logP - ilog2c(pl->C);
   a.hw = pl->d_hw;
   a.tw = TwiddleTables{pl->d_tw_lo, pl->d_tw_hi, pl->tw_lb};
+  a.tw_off = pl->slice_tw_off;
   a.ola_patch = ws.ola_patch;
   a.ola_cnt = ws.ola_cnt;
   return a;
