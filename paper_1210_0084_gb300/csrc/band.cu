@@ -21,7 +21,10 @@
 namespace slicq {
 namespace {
 
-constexpr int kTwSmall = 1024;  // W_1024 table: twiddles of every band length
+// Pass-2 twiddles of every band length M = 2^LOGM (LOGM = 4..10): entry
+// (M - 16) + r R1 + j holds exp(-2 pi i j r / M), r < R2, j < R1, so that the
+// threads of a team (consecutive j) read consecutive words.
+constexpr int kTwSmall = 2032;
 
 struct BandArgs {
   const BandDesc* __restrict__ bands;
@@ -29,7 +32,7 @@ struct BandArgs {
   const BoundaryDesc* __restrict__ bounds;
   const int16_t* __restrict__ thread_band;
   const float* __restrict__ win;     // window table of this launch
-  const float2* __restrict__ tw1024; // exp(-2 pi i t / 1024), t < 1024
+  const float2* __restrict__ twband; // pass-2 twiddle tables, kTwSmall entries
   float2* spec;                      // [slice][spec_stride]
   int64_t slice_base;                // first slice of this launch
   int64_t spec_stride;
@@ -42,15 +45,15 @@ struct BandArgs {
 };
 
 __device__ __forceinline__ void load_twiddles(const BandArgs& a, float2* s_tw) {
-  for (int i = threadIdx.x; i < kTwSmall; i += blockDim.x) s_tw[i] = __ldg(a.tw1024 + i);
+  for (int i = threadIdx.x; i < kTwSmall; i += blockDim.x) s_tw[i] = __ldg(a.twband + i);
 }
 
-// exp(SIGN 2 pi i x / 2^LOGM) from the shared W_1024 table
+// exp(SIGN 2 pi i j r / 2^LOGM) from the shared pass-2 tables
 template <int LOGM, int SIGN>
 struct BandTw {
   const float2* s_tw;
-  __device__ __forceinline__ float2 operator()(int x) const {
-    const float2 w = s_tw[x << (10 - LOGM)];
+  __device__ __forceinline__ float2 operator()(int j, int r) const {
+    const float2 w = s_tw[((1 << LOGM) - 16) + r * Team<LOGM>::R1 + j];
     return SIGN < 0 ? w : c_conj(w);
   }
 };
@@ -63,13 +66,19 @@ __device__ __forceinline__ void analysis_pass1(const BandArgs& a, const BandDesc
   constexpr int M = 1 << LOGM;
   const int twoN = 2 * a.N;
   const float* __restrict__ g = a.win + bd.win_off;
+  // branch-free: every load is issued, out-of-support residues get weight 0
+  // (the window table has padding after its last channel)
   auto load = [&](int idx) -> float2 {
     const int o = (idx - bd.j0) & (M - 1);
-    if (o >= bd.len) return make_float2(0.f, 0.f);
-    int b = bd.j0 + o;
+    const bool in = o < bd.len;
+    const int oc = in ? o : 0;
+    int b = bd.j0 + oc;
     if (b >= twoN) b -= twoN;
-    const float2 x = (b <= a.N) ? X[b] : c_conj(X[twoN - b]);
-    return c_scale(x, __ldg(g + o));
+    const bool mir = b > a.N;
+    float2 x = X[mir ? twoN - b : b];
+    const float w = __ldg(g + oc);
+    if (mir) x.y = -x.y;
+    return c_scale(x, in ? w : 0.f);
   };
   team_pass1<LOGM, +1>(tt, buf, load);
 }
@@ -312,7 +321,7 @@ BandArgs make_args(const slicq_plan* pl, const Workspace& ws, const float* win) 
   a.bounds = pl->d_bounds;
   a.thread_band = pl->d_thread_band;
   a.win = win;
-  a.tw1024 = pl->d_tw1024;
+  a.twband = pl->d_twband;
   a.spec = ws.spec;
   a.spec_stride = ws.spec_stride;
   a.cps = pl->coefs_per_slice;

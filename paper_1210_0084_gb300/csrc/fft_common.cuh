@@ -136,29 +136,33 @@ struct Team {
   static constexpr int J1 = R2 / TT;    // pass-1 sub-transforms per thread
   static constexpr int J2 = R1 / TT;    // pass-2 sub-transforms per thread
   static constexpr int HELD = J2 * R2;  // values held after pass 2
-  static constexpr int BUF = L + R2;    // padded buffer length (complex)
+  static constexpr int BUF = L + R2 + 1;  // padded buffer length (complex), odd
   __device__ __forceinline__ static int pad1(int j, int r) { return j * (R1 + 1) + r; }
   __device__ __forceinline__ static int pad2(int j, int r) { return j + r * (R1 + 1); }
 };
 
-// Pass 1: LOAD(idx) gives input element idx (0 <= idx < L).
+// Pass 1: LOAD(idx) gives input element idx (0 <= idx < L).  All of the
+// thread's loads are issued before the first DFT so that they are in flight
+// together.
 template <int LOGL, int SIGN, class Load>
 __device__ __forceinline__ void team_pass1(int tt, float2* __restrict__ buf, Load load) {
   using T = Team<LOGL>;
+  float2 v[T::J1][T::R1];
+#pragma unroll
+  for (int i = 0; i < T::J1; ++i)
+#pragma unroll
+    for (int r = 0; r < T::R1; ++r) v[i][r] = load(tt + T::TT * i + r * T::R2);
 #pragma unroll
   for (int i = 0; i < T::J1; ++i) {
     const int j = tt + T::TT * i;
-    float2 v[T::R1];
+    dft_reg<T::R1, SIGN>(v[i]);
 #pragma unroll
-    for (int r = 0; r < T::R1; ++r) v[r] = load(j + r * T::R2);
-    dft_reg<T::R1, SIGN>(v);
-#pragma unroll
-    for (int r = 0; r < T::R1; ++r) buf[T::pad1(j, r)] = v[r];
+    for (int r = 0; r < T::R1; ++r) buf[T::pad1(j, r)] = v[i][r];
   }
 }
 
 // Pass 2 (read half): twiddled, transformed values into res[i * R2 + r] for
-// element (tt + TT i) + r R1.  TW(x) returns exp(SIGN 2 pi i x / Lf).
+// element (tt + TT i) + r R1.  TW(j, r) returns exp(SIGN 2 pi i j r / Lf).
 template <int LOGL, int SIGN, class Tw>
 __device__ __forceinline__ void team_pass2(int tt, const float2* __restrict__ buf, Tw tw,
                                            float2* __restrict__ res) {
@@ -170,7 +174,7 @@ __device__ __forceinline__ void team_pass2(int tt, const float2* __restrict__ bu
 #pragma unroll
     for (int r = 0; r < T::R2; ++r) {
       float2 x = buf[T::pad2(j, r)];
-      if (r > 0) x = c_mul(x, tw(j * r));
+      if (r > 0) x = c_mul(x, tw(j, r));
       v[r] = x;
     }
     dft_reg<T::R2, SIGN>(v);

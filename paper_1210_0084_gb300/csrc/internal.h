@@ -89,7 +89,8 @@ struct slicq_plan {
   float* d_hw = nullptr;    // Tukey transition, M + 1 values
   float2* d_tw_lo = nullptr;  // exp(-2 pi i t / 2N), t < 2^tw_lb
   float2* d_tw_hi = nullptr;  // exp(-2 pi i (t << tw_lb) / 2N)
-  float2* d_tw1024 = nullptr; // exp(-2 pi i t / 1024), t < 1024
+  float2* d_twband = nullptr; // band pass-2 twiddles, per length, [r][j] layout
+  float2* d_tw4 = nullptr;    // four-step twiddles exp(-2 pi i q u / N) at [u Q + q]
 
   // optional kernel timing trace (events around every launch)
   struct Trace {

@@ -154,7 +154,7 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
         const int lm = pl->bands[k].log2M;
         const int M = 1 << lm;
         const int need_t = M >= kPerThread ? M / kPerThread : 1;
-        const int need_s = M + (M >> ((lm + 1) / 2));
+        const int need_s = M + (M >> ((lm + 1) / 2)) + 1;  // Team<lm>::BUF
         if (threads + need_t > kBandThreads) break;
         pl->bands[k].tofs = threads;
         pl->bands[k].smem_off = smem;
@@ -343,26 +343,38 @@ __global__ void k_duals(const WinJob* jobs, int nch, int64_t total, const double
   gadj[i] = (float)(0.5 * g * s);
 }
 
-// exp(-2 pi i t / L2): fine table t < 2^lb, coarse table (t << lb); and
-// exp(-2 pi i t / 1024) for the band transforms
-__global__ void k_twiddles(int64_t L2, int lb, float2* lo, float2* hi, float2* t1024) {
+// exp(-2 pi i t / L2): fine table t < 2^lb, coarse table (t << lb); the
+// pass-2 tables of the band lengths 16..1024 ([r][j] per length); and the
+// four-step twiddles exp(-2 pi i q u / N) at [u Q + q]
+__global__ void k_twiddles(int64_t L2, int lb, int logQ, float2* lo, float2* hi, float2* tband,
+                           float2* t4) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < 1024) {
-    double s, c;
-    sincospi(-2.0 * (double)i / 1024.0, &s, &c);
-    t1024[i] = make_float2((float)c, (float)s);
-  }
   const int64_t nlo = int64_t(1) << lb;
   const int64_t nhi = L2 >> lb;
+  const int64_t N = L2 / 2;
+  double s, c;
   if (i < nlo) {
-    double s, c;
     sincospi(-2.0 * (double)i / (double)L2, &s, &c);
     lo[i] = make_float2((float)c, (float)s);
   }
   if (i < nhi) {
-    double s, c;
     sincospi(-2.0 * (double)(i << lb) / (double)L2, &s, &c);
     hi[i] = make_float2((float)c, (float)s);
+  }
+  if (i < 2032) {
+    int lm = 4;
+    while (((int64_t(1) << (lm + 1)) - 16) <= i) ++lm;
+    const int64_t M = int64_t(1) << lm;
+    const int64_t R1 = int64_t(1) << ((lm + 1) / 2);
+    const int64_t e = i - (M - 16);
+    const int64_t r = e / R1, j = e % R1;
+    sincospi(-2.0 * (double)((j * r) % M) / (double)M, &s, &c);
+    tband[i] = make_float2((float)c, (float)s);
+  }
+  if (i < N) {
+    const int64_t u = i >> logQ, q = i & ((int64_t(1) << logQ) - 1);
+    sincospi(-2.0 * (double)((q * u) % N) / (double)N, &s, &c);
+    t4[i] = make_float2((float)c, (float)s);
   }
 }
 
@@ -389,13 +401,14 @@ slicq_status build_tables(slicq_plan* pl) {
   const size_t o_groups = take(sizeof(GroupDesc) * pl->G);
   const size_t o_bounds = take(sizeof(BoundaryDesc) * pl->bounds.size());
   const size_t o_tb = take(sizeof(int16_t) * pl->thread_band.size());
-  const size_t o_ga = take(sizeof(float) * std::max<int64_t>(pl->win_total, 1));
-  const size_t o_gs = take(sizeof(float) * std::max<int64_t>(pl->win_total, 1));
-  const size_t o_gadj = take(sizeof(float) * std::max<int64_t>(pl->win_total, 1));
+  const size_t o_ga = take(sizeof(float) * (pl->win_total + 32));  // + padding
+  const size_t o_gs = take(sizeof(float) * (pl->win_total + 32));  // + padding
+  const size_t o_gadj = take(sizeof(float) * (pl->win_total + 32));  // + padding
   const size_t o_hw = take(sizeof(float) * (Mtr + 1));
   const size_t o_twlo = take(sizeof(float2) * (size_t(1) << pl->tw_lb));
   const size_t o_twhi = take(sizeof(float2) * (L2 >> pl->tw_lb));
-  const size_t o_tw1024 = take(sizeof(float2) * 1024);
+  const size_t o_twband = take(sizeof(float2) * 2032);
+  const size_t o_tw4 = take(sizeof(float2) * pl->N);
   if (cudaMalloc(&pl->d_arena, off) != cudaSuccess) return SLICQ_ENOMEM;
   char* base = (char*)pl->d_arena;
   pl->d_bands = (BandDesc*)(base + o_bands);
@@ -408,7 +421,8 @@ slicq_status build_tables(slicq_plan* pl) {
   pl->d_hw = (float*)(base + o_hw);
   pl->d_tw_lo = (float2*)(base + o_twlo);
   pl->d_tw_hi = (float2*)(base + o_twhi);
-  pl->d_tw1024 = (float2*)(base + o_tw1024);
+  pl->d_twband = (float2*)(base + o_twband);
+  pl->d_tw4 = (float2*)(base + o_tw4);
 
   slicq_status st = SLICQ_OK;
   cudaError_t e = cudaSuccess;
@@ -462,9 +476,10 @@ slicq_status build_tables(slicq_plan* pl) {
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-      const int64_t nt = std::max<int64_t>(std::max<int64_t>(int64_t(1) << pl->tw_lb, L2 >> pl->tw_lb), 1024);
-      k_twiddles<<<(unsigned)((nt + T - 1) / T), T>>>(L2, pl->tw_lb, pl->d_tw_lo, pl->d_tw_hi,
-                                                      pl->d_tw1024);
+      const int64_t nt = std::max<int64_t>(std::max<int64_t>(int64_t(1) << pl->tw_lb, L2 >> pl->tw_lb),
+                                           std::max<int64_t>(2032, pl->N));
+      k_twiddles<<<(unsigned)((nt + T - 1) / T), T>>>(L2, pl->tw_lb, pl->logQ, pl->d_tw_lo, pl->d_tw_hi,
+                                                      pl->d_twband, pl->d_tw4);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) {

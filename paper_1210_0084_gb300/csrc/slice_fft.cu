@@ -40,6 +40,7 @@ struct SliceArgs {
   int C, logQc, logPc;
   const float* __restrict__ hw;   // Tukey transition, Mtr + 1 values
   TwiddleTables tw;               // global two-level tables (copied to shared memory)
+  const float2* __restrict__ tw4; // four-step twiddles exp(-2 pi i q u / N) at [u Q + q]
   int tw_off;                     // shared-memory offset (float2) of the table copy
   float* ola_patch;               // [slice][2][Mtr]
   uint32_t* ola_cnt;              // [slice][C]
@@ -60,9 +61,9 @@ struct Geo {
   static constexpr int P = 1 << LOGP, Q = 1 << LOGQ;
   using TP = Team<LOGP>;
   using TQ = Team<LOGQ>;
-  static constexpr int CS1 = TP::BUF + 1;  // odd column stride of pass buffers
+  static constexpr int CS1 = TP::BUF;      // odd column stride of pass buffers
   static constexpr int XS1 = P + 1;        // column stride of the exchange layout
-  static constexpr int CS3 = TQ::BUF + 1;
+  static constexpr int CS3 = TQ::BUF;
   static constexpr int ZS3 = Q + 1;
 };
 
@@ -71,11 +72,11 @@ struct Geo {
 // Z[u + P v] for u = rank * P/C + ul, v = (tt + TTq i) + r R1q, and the shared
 // memory may be reused after a __syncthreads().
 template <int SIGN>
-struct SliceTw {  // exp(SIGN 2 pi i x / 2^(log2N2 - shift)) from the shared tables
+struct SliceTw {  // exp(SIGN 2 pi i j r / 2^(log2N2 - shift)) from the shared tables
   SmemTwiddles t;
   int shift;
-  __device__ __forceinline__ float2 operator()(int x) const {
-    const float2 w = t((uint32_t)x << shift);
+  __device__ __forceinline__ float2 operator()(int j, int r) const {
+    const float2 w = t((uint32_t)(j * r) << shift);
     return SIGN < 0 ? w : c_conj(w);
   }
 };
@@ -120,10 +121,9 @@ __device__ __forceinline__ void fourstep(const SliceArgs& a, cg::cluster_group& 
 #pragma unroll
       for (int r = 0; r < TP::R2; ++r) {
         const int u = team_out_index<LOGP>(tt, i, r);
-        float2 v = col[i * TP::R2 + r];
-        const uint32_t e = ((uint32_t)(q * u) & ((1u << (LOGP + LOGQ)) - 1u)) << 1;
-        if (e) v = c_mul(v, SliceTw<SIGN>{tws, 0}((int)e));
-        sm[ql * G::XS1 + u] = v;
+        float2 w = __ldg(a.tw4 + u * G::Q + q);
+        if (SIGN > 0) w.y = -w.y;
+        sm[ql * G::XS1 + u] = c_mul(col[i * TP::R2 + r], w);
       }
   }
   cluster.sync();
@@ -180,13 +180,19 @@ __global__ void __launch_bounds__(kSliceMaxThreads, 2) slice_forward_kernel(Slic
   const float* f = a.f + b * a.n;
   const int64_t base = (int64_t)(m - 1) * a.N;
 
+  // branch-free: both loads are always issued (clamped indices), the window
+  // is 0 outside the support of h_0 and past the end of the signal
+  const int a0 = (a.N - a.Mtr) >> 1;
   auto sample = [&](int j) -> float {
-    const float w = slicing_window(a, j);
-    if (w == 0.f) return 0.f;
+    const int d = abs(j - a.N);
+    const float ht = __ldg(a.hw + min(max(d - a0, 0), a.Mtr));
+    float w = d <= a0 ? 1.f : (2 * d < a.N + a.Mtr ? ht : 0.f);
     int64_t tpos = base + j;
     if (tpos < 0) tpos += a.L;
     if (tpos >= a.L) tpos -= a.L;
-    return tpos < a.n ? __ldg(f + tpos) * w : 0.f;
+    const bool in = tpos < a.n;
+    const float x = __ldg(f + (in ? tpos : 0));
+    return in ? x * w : 0.f;
   };
   auto load = [&](int e) -> float2 { return make_float2(sample(2 * e), sample(2 * e + 1)); };
 
@@ -407,6 +413,7 @@ SliceArgs make_args(const slicq_plan* pl, const Workspace& ws, int64_t n) {
   a.hw = pl->d_hw;
   a.tw = TwiddleTables{pl->d_tw_lo, pl->d_tw_hi, pl->tw_lb};
   a.tw_off = pl->slice_tw_off;
+  a.tw4 = pl->d_tw4;
   a.ola_patch = ws.ola_patch;
   a.ola_cnt = ws.ola_cnt;
   return a;
