@@ -196,6 +196,28 @@ SLICQ_API slicq_status slicq_plan_table(const slicq_plan* plan, int32_t which,
                               float* h_out, int64_t count, int64_t* n_out);
 
 /*
+ * Forward sliCQ without a caller workspace and without allocating (the paper
+ * has no counterpart: this serves callers that may not allocate device
+ * memory, such as real-time audio callbacks that must not block on an
+ * allocator, or plug-in hosts that own all device memory).
+ *   Same arguments and result as slicq_forward, minus the workspace.  The
+ *   slice spectra go to a fixed 32 MiB array compiled into the library,
+ *   which every GPU that loads the library holds until the process exits.
+ *   Returns SLICQ_ESIZE when batch * slicq_num_slices(n_samples) * (N + 2)
+ *   complex values (8 bytes each) exceed 32 MiB, and the usual errors
+ *   otherwise.  It calls no cudaMalloc, cudaFree or other allocating routine.
+ *   The first call on a device looks up the array's device address (once per
+ *   device, with the plan's device current); make that first call before
+ *   any stream capture.  All calls share the array and it keeps the last
+ *   call's contents, so calls that overlap on the GPU (other streams, other
+ *   threads, other plans) race and must be serialised by the caller.
+ */
+SLICQ_API slicq_status slicq_forward_noalloc(const slicq_plan* plan, const float* d_f,
+                                             int64_t n_samples, int64_t batch,
+                                             float* d_coef, int64_t coef_capacity,
+                                             cudaStream_t stream);
+
+/*
  * Kernel timing trace (diagnostics and benchmarking; not part of the
  * paper's method).  With enable != 0 every later forward / inverse /
  * adjoint call on this plan records a CUDA event on its stream before and
