@@ -74,6 +74,7 @@ size_t workspace_layout(const slicq_plan* pl, int64_t n, int64_t batch, void* ba
   const int64_t nbd = std::max(pl->G - 1, 0);
   size_t off = 0;
   auto take = [&](size_t bytes) { const size_t o = off; off = align256(off + bytes); return o; };
+  const size_t o_items = take(2 * sizeof(unsigned long long));
   const size_t o_spec = take(sizeof(float2) * slices * w.spec_stride);
   const size_t o_bp = take(sizeof(float2) * slices * nbd * 2 * pl->max_ovl);
   const size_t o_bc = take(sizeof(uint32_t) * slices * nbd);
@@ -82,6 +83,7 @@ size_t workspace_layout(const slicq_plan* pl, int64_t n, int64_t batch, void* ba
   w.bytes = off;
   if (base) {
     char* b = (char*)base;
+    w.items = (unsigned long long*)(b + o_items);
     w.spec = (float2*)(b + o_spec);
     w.band_patch = (float2*)(b + o_bp);
     w.band_cnt = (uint32_t*)(b + o_bc);
@@ -188,6 +190,7 @@ static slicq_status check_common(const slicq_plan* plan, int64_t n, int64_t batc
   if (!plan || !a || !b || !work || n < 1 || batch < 1) return SLICQ_EINVAL;
   if ((reinterpret_cast<uintptr_t>(work) & 255) != 0) return SLICQ_EINVAL;
   const size_t need = workspace_layout(plan, n, batch, work, ws);
+  if (ws->L >= (int64_t(1) << 31)) return SLICQ_EUNSUPPORTED;  // positions are 32-bit
   if (work_bytes < need) return SLICQ_ESIZE;
   return SLICQ_OK;
 }

@@ -109,6 +109,7 @@ __global__ void __launch_bounds__(kBandThreads) band_analysis_kernel(BandArgs a)
   const float2* X = a.spec + s * a.spec_stride;
   float2* buf = sm + bd.smem_off;
   load_twiddles(a, s_tw);
+  __syncthreads();  // the table is filled by all threads; the passes only sync per warp
   if (k >= 0) {
     switch (bd.log2M) {
       case 4: analysis_pass1<4>(a, bd, tt, X, buf); break;
@@ -120,7 +121,9 @@ __global__ void __launch_bounds__(kBandThreads) band_analysis_kernel(BandArgs a)
       case 10: analysis_pass1<10>(a, bd, tt, X, buf); break;
     }
   }
-  __syncthreads();
+  // a team (one channel) lies inside one warp: the groups hold channels of
+  // one length and teams start at multiples of their size
+  __syncwarp();
   if (k >= 0) {
     float2* out = a.coef + s * a.cps + bd.coef_off;
     switch (bd.log2M) {
@@ -219,6 +222,7 @@ __global__ void __launch_bounds__(kBandThreads) band_synthesis_kernel(BandArgs a
     const BandDesc b = a.bands[gd.band_begin + t];
     s_gb[t] = GatherBand{b.dlo, b.dhi, b.j0, b.smem_off};
   }
+  __syncthreads();  // tables filled by all threads; the passes only sync per warp
   if (k >= 0) {
     const float2* c = a.coef + s * a.cps + bd.coef_off;
     switch (bd.log2M) {
@@ -231,7 +235,7 @@ __global__ void __launch_bounds__(kBandThreads) band_synthesis_kernel(BandArgs a
       case 10: synthesis_pass1<10>(tt, c, buf); break;
     }
   }
-  __syncthreads();
+  __syncwarp();  // a team lies inside one warp
   float2 res[kPerThread];
   if (k >= 0) {
     switch (bd.log2M) {
@@ -244,7 +248,7 @@ __global__ void __launch_bounds__(kBandThreads) band_synthesis_kernel(BandArgs a
       case 10: synthesis_pass2<10>(tt, s_tw, buf, res); break;
     }
   }
-  __syncthreads();  // every team has read its pass buffer: reuse it for contributions
+  __syncwarp();  // the team has read its pass buffer: reuse it for contributions
   if (k >= 0) {
     switch (bd.log2M) {
       case 4: synthesis_weight<4>(a, bd, tt, res, buf); break;
@@ -296,6 +300,7 @@ __global__ void __launch_bounds__(kBandThreads) band_synthesis_kernel(BandArgs a
     if (bd_i < 0) continue;
     const BoundaryDesc b = a.bounds[bd_i];
     const int64_t slot = s * (a.G - 1) + bd_i;
+    // every thread makes its own slot writes visible before the counter moves
     __threadfence();
     __syncthreads();
     if (t == 0) {
@@ -340,13 +345,13 @@ cudaError_t launch_band_analysis(const slicq_plan* pl, const Workspace& ws, int6
   BandArgs a = make_args(pl, ws, pl->d_ga);
   a.coef = coef;
   cudaError_t e = cudaFuncSetAttribute(band_analysis_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, pl->band_smem);
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, pl->band_smem_a);
   if (e != cudaSuccess) return e;
   const int64_t total = batch * ws.S;
   for (int64_t s0 = 0; s0 < total; s0 += kMaxGridY) {
     a.slice_base = s0;
     dim3 grid(pl->G, (unsigned)(total - s0 < kMaxGridY ? total - s0 : kMaxGridY));
-    band_analysis_kernel<<<grid, kBandThreads, pl->band_smem, st>>>(a);
+    band_analysis_kernel<<<grid, kBandThreads, pl->band_smem_a, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;
@@ -357,13 +362,13 @@ cudaError_t launch_band_synthesis(const slicq_plan* pl, const float2* coef, int6
   BandArgs a = make_args(pl, ws, kind == kSynthInverse ? pl->d_gs : pl->d_gadj);
   a.coef = const_cast<float2*>(coef);
   cudaError_t e = cudaFuncSetAttribute(band_synthesis_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, pl->band_smem);
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, pl->band_smem_a);
   if (e != cudaSuccess) return e;
   const int64_t total = batch * ws.S;
   for (int64_t s0 = 0; s0 < total; s0 += kMaxGridY) {
     a.slice_base = s0;
     dim3 grid(pl->G, (unsigned)(total - s0 < kMaxGridY ? total - s0 : kMaxGridY));
-    band_synthesis_kernel<<<grid, kBandThreads, pl->band_smem, st>>>(a);
+    band_synthesis_kernel<<<grid, kBandThreads, pl->band_smem_a, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
   return cudaSuccess;

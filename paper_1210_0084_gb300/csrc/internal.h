@@ -41,6 +41,9 @@ struct GroupDesc {
   int32_t left_bd, right_bd;     // boundary indices, -1 if none
   int32_t nmirror;               // channels of the group with mirrored bins
   int32_t mirror[16];            // their indices
+  int32_t log2M;                 // every channel of the group has M = 2^log2M
+  int32_t fp_lo, fp_len;         // spectrum block the analysis stages (even bounds)
+  int32_t pad_;
 };
 
 // Bins [lo, hi) touched by two neighbouring groups (bd and bd + 1).
@@ -64,7 +67,11 @@ struct slicq_plan {
   int C = 1;              // cluster size of the slice kernels
   int G = 0;              // band groups
   int max_ovl = 0;        // longest group-boundary overlap (bins)
-  int band_smem = 0;      // dynamic shared memory of the band kernels (bytes)
+  int band_smem_a = 0;    // dynamic shared memory of band analysis (bytes)
+  int band_smem_s = 0;    // dynamic shared memory of band synthesis (bytes)
+  int band_in_a = 0;      // complex values per staged analysis input (max footprint)
+  int band_in_s = 0;      // complex values per staged synthesis input (max group block)
+  int num_sms = 152;      // SMs of the plan's device (grid sizing)
   int slice_smem = 0;     // dynamic shared memory of the slice kernels (bytes)
   int slice_tw_off = 0;   // float2 offset of the twiddle tables in that memory
   int tw_lb = 0;          // log2 of the fine twiddle table length
@@ -110,6 +117,7 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl);
 // Workspace partition for (n_samples, batch).
 struct Workspace {
   int64_t S = 0, L = 0;
+  unsigned long long* items = nullptr;  // [2] work counters of the band kernels
   int64_t spec_stride = 0;         // complex values per slice spectrum row
   float2* spec = nullptr;          // [batch * S][spec_stride]
   float2* band_patch = nullptr;    // [batch * S][G - 1][2][max_ovl]

@@ -143,7 +143,7 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
   // ---- band groups: consecutive channels, <= kBandThreads threads each
   pl->groups.clear();
   pl->thread_band.clear();
-  int band_smem_c = 0;
+  int in_a = 0, in_s = 0, tb_max = 0;  // complex values
   {
     int k = 0;
     while (k < nch) {
@@ -156,6 +156,8 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
         const int need_t = M >= kPerThread ? M / kPerThread : 1;
         const int need_s = M + (M >> ((lm + 1) / 2)) + 1;  // Team<lm>::BUF
         if (threads + need_t > kBandThreads) break;
+        // one band length per group: every warp of the CTA runs the same code
+        if (k > gd.band_begin && lm != pl->bands[gd.band_begin].log2M) break;
         pl->bands[k].tofs = threads;
         pl->bands[k].smem_off = smem;
         threads += need_t;
@@ -187,7 +189,18 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
       if (ahi < 0) return SLICQ_EINVAL;
       gd.acc_lo = alo;
       gd.acc_hi = ahi + 1;
-      band_smem_c = std::max(band_smem_c, smem);
+      gd.log2M = pl->bands[gd.band_begin].log2M;
+      gd.fp_lo = alo & ~1;
+      gd.fp_len = (gd.acc_hi - gd.fp_lo + 1) & ~1;
+      {
+        const int M = 1 << gd.log2M;
+        const int nb = gd.band_end - gd.band_begin;
+        const int bufl = M + (M >> ((gd.log2M + 1) / 2)) + 1;  // Team<log2M>::BUF
+        in_a = std::max(in_a, gd.fp_len);
+        in_s = std::max(in_s, nb * M);
+        tb_max = std::max(tb_max, nb * bufl);
+      }
+      (void)smem;
       pl->groups.push_back(gd);
       std::vector<int16_t> tb(kBandThreads, (int16_t)-1);
       for (int b = gd.band_begin; b < gd.band_end; ++b) {
@@ -233,8 +246,12 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
     gd.ex_lo = gd.left_bd >= 0 ? pl->bounds[gd.left_bd].hi : gd.acc_lo;
     gd.ex_hi = gd.right_bd >= 0 ? pl->bounds[gd.right_bd].lo : gd.acc_hi;
   }
-  pl->band_smem = band_smem_c * (int)sizeof(float2);
-  if (pl->band_smem > 200 * 1024) return SLICQ_EUNSUPPORTED;
+  pl->band_in_a = (in_a + 1) & ~1;
+  pl->band_in_s = (in_s + 1) & ~1;
+  // per-slice band kernels: one team buffer per channel of the group
+  pl->band_smem_a = tb_max * (int)sizeof(float2);
+  pl->band_smem_s = tb_max * (int)sizeof(float2);
+  if (pl->band_smem_a > 220 * 1024 || pl->band_smem_s > 220 * 1024) return SLICQ_EUNSUPPORTED;
 
   // ---- slice FFT geometry: N = P Q, cluster of C CTAs, <= 256 threads each
   const int logN = ilog2_64(N);
@@ -426,6 +443,11 @@ slicq_status build_tables(slicq_plan* pl) {
 
   slicq_status st = SLICQ_OK;
   cudaError_t e = cudaSuccess;
+  {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl->device) == cudaSuccess && sms > 0)
+      pl->num_sms = sms;
+  }
   e = cudaMemcpy(pl->d_bands, pl->bands.data(), sizeof(BandDesc) * nch, cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(pl->d_groups, pl->groups.data(), sizeof(GroupDesc) * pl->G, cudaMemcpyHostToDevice);

@@ -44,6 +44,7 @@ struct SliceArgs {
   int tw_off;                     // shared-memory offset (float2) of the table copy
   float* ola_patch;               // [slice][2][Mtr]
   uint32_t* ola_cnt;              // [slice][C]
+  unsigned long long* items;      // band-kernel work counter this launch resets
   int adjoint;                    // multiply the output by h_0 instead of 1
 };
 
@@ -51,9 +52,8 @@ struct SliceArgs {
 __device__ __forceinline__ float slicing_window(const SliceArgs& a, int j) {
   const int d = abs(j - a.N);
   const int a0 = (a.N - a.Mtr) >> 1;
-  if (d <= a0) return 1.f;
-  if (2 * d < a.N + a.Mtr) return __ldg(a.hw + (d - a0));
-  return 0.f;
+  const float ht = __ldg(a.hw + min(max(d - a0, 0), a.Mtr));
+  return d <= a0 ? 1.f : (2 * d < a.N + a.Mtr ? ht : 0.f);
 }
 
 template <int LOGP, int LOGQ>
@@ -178,24 +178,33 @@ __global__ void __launch_bounds__(kSliceMaxThreads, 2) slice_forward_kernel(Slic
   const int64_t b = s / a.S;
   const int m = (int)(s - b * a.S);
   const float* f = a.f + b * a.n;
-  const int64_t base = (int64_t)(m - 1) * a.N;
+  const int n32 = (int)a.n, L32 = (int)a.L;   // the entry points keep L < 2^31
+  const int base = (m - 1) * a.N;             // position of slice sample 0 (slice 0: -N)
+  const bool vec = ((b * a.n) & 1) == 0;      // f is 8-byte aligned (uniform per CTA)
 
-  // branch-free: both loads are always issued (clamped indices), the window
-  // is 0 outside the support of h_0 and past the end of the signal
-  const int a0 = (a.N - a.Mtr) >> 1;
-  auto sample = [&](int j) -> float {
-    const int d = abs(j - a.N);
-    const float ht = __ldg(a.hw + min(max(d - a0, 0), a.Mtr));
-    float w = d <= a0 ? 1.f : (2 * d < a.N + a.Mtr ? ht : 0.f);
-    int64_t tpos = base + j;
-    if (tpos < 0) tpos += a.L;
-    if (tpos >= a.L) tpos -= a.L;
-    const bool in = tpos < a.n;
-    const float x = __ldg(f + (in ? tpos : 0));
-    return in ? x * w : 0.f;
+  // Element e of the packed slice is (x[2e], x[2e+1]); x[j] = f[j + (m-1)N] h_0[j-N].
+  // Branch-free: every load is issued with a clamped index and weighted by 0
+  // outside the support of h_0 and past the end of the signal.
+  auto load = [&](int e) -> float2 {
+    const int j = 2 * e;
+    const float w0 = slicing_window(a, j), w1 = slicing_window(a, j + 1);
+    int t = base + j;
+    if (t < 0) t += L32; else if (t >= L32) t -= L32;   // t even, t + 1 < L
+    const bool in0 = t < n32, in1 = t + 1 < n32;
+    float2 x;
+    if (vec && in1) {
+      x = __ldg(reinterpret_cast<const float2*>(f + t));
+    } else {
+      x.x = __ldg(f + (in0 ? t : 0));
+      x.y = __ldg(f + (in1 ? t + 1 : 0));
+    }
+    x.x = in0 ? x.x * w0 : 0.f;
+    x.y = in1 ? x.y * w1 : 0.f;
+    return x;
   };
-  auto load = [&](int e) -> float2 { return make_float2(sample(2 * e), sample(2 * e + 1)); };
 
+  // the band analysis that follows in the same stream counts its work items from 0
+  if (blockIdx.x == 0 && threadIdx.x == 0) *a.items = 0ull;
   const SmemTwiddles tws = stage_twiddles(a, sm);
   __syncthreads();
   {
@@ -248,7 +257,7 @@ __device__ __forceinline__ void ola_combine(const SliceArgs& a, int64_t tr_slot,
                                             int rank, int* s_flag, float* out, Each each) {
   float* mine = a.ola_patch + (tr_slot * 2 + side) * (int64_t)a.Mtr;
   const float* other = a.ola_patch + (tr_slot * 2 + (1 - side)) * (int64_t)a.Mtr;
-  each([&](int o, int64_t tpos, float v) { mine[o] = v; });
+  each([&](int o, int tpos, float v) { mine[o] = v; });
   __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) {
@@ -258,7 +267,7 @@ __device__ __forceinline__ void ola_combine(const SliceArgs& a, int64_t tr_slot,
   __syncthreads();
   if (*s_flag) {
     __threadfence();
-    each([&](int o, int64_t tpos, float v) {
+    each([&](int o, int tpos, float v) {
       if (tpos < a.n) out[tpos] = v + __ldcg(other + o);
     });
   }
@@ -278,6 +287,9 @@ __global__ void __launch_bounds__(kSliceMaxThreads) slice_inverse_kernel(SliceAr
   const float2* H = a.spec + s * a.spec_stride;
   const int N = a.N;
 
+  // the band synthesis of the next call counts its work items from 0 (it has
+  // finished for this call: it precedes this kernel in the stream)
+  if (blockIdx.x == 0 && threadIdx.x == 0) *a.items = 0ull;
   const SmemTwiddles tws = stage_twiddles(a, sm);
   __syncthreads();
   // Z[k] = (H[k] + conj H[N-k]) + i e^{+2 pi i k / 2N} (H[k] - conj H[N-k])
@@ -301,58 +313,71 @@ __global__ void __launch_bounds__(kSliceMaxThreads) slice_inverse_kernel(SliceAr
   }
   __syncthreads();
 
-  // time samples 2n, 2n+1 with n = u + P v; this CTA holds u in [rank Pc, (rank+1) Pc)
+  // Time samples 2n, 2n+1 of z[n], n = u + P v; this CTA holds u in
+  // [rank Pc, (rank+1) Pc).  Each region of the slice (where only this slice
+  // contributes; the right and left transitions) is visited over its own
+  // index range.
   const int Pc = 1 << a.logPc;
   const int rank = (int)cluster.block_rank();
   const int a0 = (N - a.Mtr) >> 1;
-  const int64_t base = (int64_t)(m - 1) * N;
+  const int n32 = (int)a.n, L32 = (int)a.L;
+  const int base = (m - 1) * N;
   float* out = a.out + b * a.n;
-  const int held = Pc * G::Q;
-  auto tpos_of = [&](int j) -> int64_t {
-    int64_t tp = base + j;
-    if (tp < 0) tp += a.L;
-    if (tp >= a.L) tp -= a.L;
-    return tp;
+  auto tpos_of = [&](int j) -> int {
+    int t = base + j;
+    if (t < 0) t += L32; else if (t >= L32) t -= L32;
+    return t;
   };
-  auto sample = [&](int idx, int h, int& j) -> float {
-    const int ul = idx & (Pc - 1);
-    const int v = idx >> a.logPc;
-    const float2 z = sm[ul * G::ZS3 + v];
-    j = 2 * (rank * Pc + ul + G::P * v) + h;
-    const float x = h ? z.y : z.x;
-    return a.adjoint ? x * slicing_window(a, j) : x;
+  auto weighted = [&](int j, float x) -> float { return a.adjoint ? x * slicing_window(a, j) : x; };
+  // fn(n, z) for the held elements with n0 <= n < n1
+  auto for_range = [&](int n0, int n1, auto&& fn) {
+    if (n0 >= n1) return;
+    const int v0 = n0 >> LOGP, v1 = (n1 - 1) >> LOGP;
+    const int cnt = (v1 - v0 + 1) << a.logPc;
+    for (int idx = threadIdx.x; idx < cnt; idx += blockDim.x) {
+      const int ul = idx & (Pc - 1);
+      const int v = v0 + (idx >> a.logPc);
+      const int n = rank * Pc + ul + (v << LOGP);
+      if (n >= n0 && n < n1) fn(n, sm[ul * G::ZS3 + v]);
+    }
   };
 
-  // samples where only this slice contributes
-  for (int idx = threadIdx.x; idx < held; idx += blockDim.x)
+  // samples with |j - N| <= a0: only this slice contributes
+  for_range((N - a0) >> 1, ((N + a0) >> 1) + 1, [&](int n, float2 z) {
+#pragma unroll
     for (int h = 0; h < 2; ++h) {
-      int j;
-      const float x = sample(idx, h, j);
+      const int j = 2 * n + h;
       if (abs(j - N) <= a0) {
-        const int64_t tp = tpos_of(j);
-        if (tp < a.n) out[tp] = x;
+        const int t = tpos_of(j);
+        if (t < n32) out[t] = weighted(j, h ? z.y : z.x);
       }
     }
+  });
 
-  // right transition (shared with slice m+1; this slice is side 0) and left
-  // transition (shared with slice m-1; side 1), offsets o in [1, M-1]
+  // transitions, offsets o in [1, M-1]: right (j - N = a0 + o, shared with
+  // slice m+1, this slice is side 0) and left (j = a0 + o, shared with slice
+  // m-1, side 1)
+  const int rn0 = (N + a0 + 1) >> 1, rn1 = ((N + a0 + a.Mtr - 1) >> 1) + 1;
+  const int ln0 = (a0 + 1) >> 1, ln1 = ((a0 + a.Mtr - 1) >> 1) + 1;
   auto each_right = [&](auto&& fn) {
-    for (int idx = threadIdx.x; idx < held; idx += blockDim.x)
+    for_range(rn0, rn1, [&](int n, float2 z) {
+#pragma unroll
       for (int h = 0; h < 2; ++h) {
-        int j;
-        const float x = sample(idx, h, j);
-        const int d = j - N;
-        if (d > a0 && 2 * d < N + a.Mtr) fn(d - a0, tpos_of(j), x);
+        const int j = 2 * n + h;
+        const int o = j - N - a0;
+        if (o > 0 && o < a.Mtr) fn(o, tpos_of(j), weighted(j, h ? z.y : z.x));
       }
+    });
   };
   auto each_left = [&](auto&& fn) {
-    for (int idx = threadIdx.x; idx < held; idx += blockDim.x)
+    for_range(ln0, ln1, [&](int n, float2 z) {
+#pragma unroll
       for (int h = 0; h < 2; ++h) {
-        int j;
-        const float x = sample(idx, h, j);
-        const int d = N - j;
-        if (d > a0 && 2 * d < N + a.Mtr) fn(j - a0, tpos_of(j), x);
+        const int j = 2 * n + h;
+        const int o = j - a0;
+        if (o > 0 && o < a.Mtr) fn(o, tpos_of(j), weighted(j, h ? z.y : z.x));
       }
+    });
   };
   const int64_t bS = b * a.S;
   ola_combine(a, bS + m, 0, rank, &s_flag, out, each_right);
@@ -425,6 +450,7 @@ cudaError_t launch_slice_forward(const slicq_plan* pl, const float* f, int64_t n
                                  const Workspace& ws, cudaStream_t st) {
   SliceArgs a = make_args(pl, ws, n);
   a.f = f;
+  a.items = ws.items + 0;
   return dispatch(true, pl, a, batch * ws.S, st);
 }
 
@@ -432,6 +458,7 @@ cudaError_t launch_slice_inverse(const slicq_plan* pl, int64_t n, int64_t batch,
                                  const Workspace& ws, float* out, cudaStream_t st) {
   SliceArgs a = make_args(pl, ws, n);
   a.out = out;
+  a.items = ws.items + 1;
   a.adjoint = kind == kSynthAdjoint;
   return dispatch(false, pl, a, batch * ws.S, st);
 }
