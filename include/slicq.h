@@ -28,7 +28,8 @@
  *   - Calls that take a stream are asynchronous on that stream.  They return
  *     argument errors before launching anything and launch errors at once;
  *     faults inside a kernel surface at the next synchronising call.
- *   - No entry point allocates device memory except slicq_plan_create.
+ *   - No entry point allocates device memory except slicq_plan_create and
+ *     slicq_batch_create.
  *   - Nothing throws across the ABI; every call returns a slicq_status.
  */
 #ifndef SLICQ_H
@@ -194,6 +195,44 @@ SLICQ_API slicq_status slicq_adjoint(const slicq_plan* plan, const float* d_coef
  */
 SLICQ_API slicq_status slicq_plan_table(const slicq_plan* plan, int32_t which,
                               float* h_out, int64_t count, int64_t* n_out);
+
+/*
+ * Ragged batches (not in the paper, whose slices are independent, Sec. 4):
+ * many clips of different lengths, sample rates and bins per octave in one
+ * call.  Every plan of a batch must have the same slice_len and trans_len
+ * and live on the same device (SLICQ_EUNSUPPORTED otherwise).
+ *   plans[p]          p < n_plans, owned by the caller, alive while the
+ *                     batch is used
+ *   clip_plan[c]      plan of clip c, clip_samples[c] its length (>= 1)
+ * slicq_batch_create allocates the batch's row tables on the device and
+ * creates one stream per plan; each call forks the plans' kernel chains from
+ * the caller's stream and joins them back, so capturing one call in a CUDA
+ * graph records the whole batch (plans as parallel branches).
+ * Layouts (queried with slicq_batch_layout, host arrays of n_clips entries):
+ *   signals       one float buffer; clip c at h_sig_off[c] (multiple of 4
+ *                 samples), sig_total floats in all, 16-byte aligned base
+ *   coefficients  one interleaved complex buffer; clip c's slices
+ *                 (h_slices[c] of them, its plan's coefs_per_slice each) at
+ *                 h_coef_off[c] complex values; coef_total in all
+ *   workspace     work_bytes, 256-byte aligned, zero-filled once
+ */
+typedef struct slicq_batch slicq_batch;
+SLICQ_API slicq_status slicq_batch_create(const slicq_plan* const* plans, int32_t n_plans,
+                                          const int32_t* clip_plan, const int64_t* clip_samples,
+                                          int32_t n_clips, slicq_batch** out);
+SLICQ_API void slicq_batch_destroy(slicq_batch* batch);
+SLICQ_API slicq_status slicq_batch_layout(const slicq_batch* batch, int64_t* h_sig_off,
+                                          int64_t* h_coef_off, int64_t* h_slices,
+                                          int64_t* sig_total, int64_t* coef_total,
+                                          size_t* work_bytes);
+/* Forward (Algorithm 3) of every clip of the batch. */
+SLICQ_API slicq_status slicq_batch_forward(const slicq_batch* batch, const float* d_sig,
+                                           float* d_coef, void* d_work, size_t work_bytes,
+                                           cudaStream_t stream);
+/* Inverse (Algorithm 4) of every clip; writes each clip's samples at its offset. */
+SLICQ_API slicq_status slicq_batch_inverse(const slicq_batch* batch, const float* d_coef,
+                                           float* d_sig_out, void* d_work, size_t work_bytes,
+                                           cudaStream_t stream);
 
 /*
  * Forward sliCQ without a caller workspace and without allocating (the paper

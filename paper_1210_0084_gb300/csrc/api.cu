@@ -94,6 +94,34 @@ size_t workspace_layout(const slicq_plan* pl, int64_t n, int64_t batch, void* ba
   return off;
 }
 
+size_t workspace_layout_rows(const slicq_plan* pl, int64_t rows, void* base, Workspace* ws) {
+  Workspace w;
+  w.S = rows;
+  w.L = 0;
+  w.spec_stride = pl->N + 2;
+  const int64_t nbd = std::max(pl->G - 1, 0);
+  size_t off = 0;
+  auto take = [&](size_t bytes) { const size_t o = off; off = align256(off + bytes); return o; };
+  const size_t o_items = take(2 * sizeof(unsigned long long));
+  const size_t o_spec = take(sizeof(float2) * rows * w.spec_stride);
+  const size_t o_bp = take(sizeof(float2) * rows * nbd * 2 * pl->max_ovl);
+  const size_t o_bc = take(sizeof(uint32_t) * rows * nbd);
+  const size_t o_op = take(sizeof(float) * rows * 2 * pl->params.trans_len);
+  const size_t o_oc = take(sizeof(uint32_t) * rows * pl->C);
+  w.bytes = off;
+  if (base) {
+    char* b = (char*)base;
+    w.items = (unsigned long long*)(b + o_items);
+    w.spec = (float2*)(b + o_spec);
+    w.band_patch = (float2*)(b + o_bp);
+    w.band_cnt = (uint32_t*)(b + o_bc);
+    w.ola_patch = (float*)(b + o_op);
+    w.ola_cnt = (uint32_t*)(b + o_oc);
+  }
+  if (ws) *ws = w;
+  return off;
+}
+
 }  // namespace slicq
 
 using namespace slicq;

@@ -31,10 +31,12 @@ struct BandArgs {
   const GroupDesc* __restrict__ groups;
   const BoundaryDesc* __restrict__ bounds;
   const int16_t* __restrict__ thread_band;
+  const int32_t* __restrict__ mirror_list;  // channels with mirrored bins, per group
   const float* __restrict__ win;     // window table of this launch
   const float2* __restrict__ twband; // pass-2 twiddle tables, kTwSmall entries
   float2* spec;                      // [slice][spec_stride]
-  int64_t slice_base;                // first slice of this launch
+  int64_t slice_base;                // first slice of this launch (per-slice kernels)
+  int64_t total;                     // slices of the call (persistent kernel)
   int64_t spec_stride;
   float2* coef;                      // [slice][cps]
   int64_t cps;
@@ -138,6 +140,106 @@ __global__ void __launch_bounds__(kBandThreads) band_analysis_kernel(BandArgs a)
   }
 }
 
+// --------------------------------------------------------------- cp.async ---
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory");
+}
+
+// ------------------------------------------------------------ analysis ---
+// Persistent form: CTA c keeps group cta_group[c] and walks the slices
+// s = lane, lane + lanes, ... (lanes per group proportional to the group's
+// work).  Each slice's footprint of the spectrum [fp_lo, fp_lo + fp_len) is
+// one contiguous block; cp.async copies the next slice's block while the
+// current one is transformed.  Shared memory: [twiddles M][footprint x 2]
+// [team buffers].
+
+template <int LOGM>
+__device__ void analysis_persistent(const BandArgs& a, const GroupDesc& gd, int lane, int lanes,
+                                    int64_t total, float2* sm) {
+  using T = Team<LOGM>;
+  constexpr int M = 1 << LOGM;
+  const int t = threadIdx.x;
+  const int nb = gd.band_end - gd.band_begin;
+  const int bl = t / T::TT;
+  const int tt = t - bl * T::TT;
+  const bool active = bl < nb;
+  const BandDesc bd = a.bands[gd.band_begin + (active ? bl : 0)];
+  const int twoN = 2 * a.N;
+  float2* s_tw = sm;
+  float2* s_x0 = sm + M;
+  float2* s_x1 = s_x0 + gd.fp_len;
+  float2* buf = s_x1 + gd.fp_len + bl * T::BUF;
+  const float* __restrict__ g = a.win + bd.win_off;
+  for (int i = t; i < M; i += blockDim.x) s_tw[i] = __ldg(a.twband + (M - 16) + i);
+  auto stage = [&](int64_t s, float2* dst) {
+    const float2* src = a.spec + s * a.spec_stride + gd.fp_lo;
+    for (int i = 2 * t; i < gd.fp_len; i += 2 * (int)blockDim.x) cp_async16(dst + i, src + i);
+  };
+  int64_t s = lane;
+  if (s < total) stage(s, s_x0);
+  cp_async_commit();
+  for (int it = 0; s < total; s += lanes, ++it) {
+    const float2* X = ((it & 1) ? s_x1 : s_x0) - gd.fp_lo;  // X[b] for b in the footprint
+    if (s + lanes < total) stage(s + lanes, (it & 1) ? s_x0 : s_x1);
+    cp_async_commit();
+    cp_async_wait<1>();
+    __syncthreads();  // this slice's block (and, first time, the twiddles) are in
+    if (active) {
+      // every load is issued; out-of-support residues get weight 0 (the
+      // window table has padding after its last channel)
+      auto load = [&](int idx) -> float2 {
+        const int o = (idx - bd.j0) & (M - 1);
+        const bool in = o < bd.len;
+        const int oc = in ? o : 0;
+        int b = bd.j0 + oc;
+        if (b >= twoN) b -= twoN;
+        const bool mir = b > a.N;
+        float2 x = X[mir ? twoN - b : b];
+        const float w = __ldg(g + oc);
+        if (mir) x.y = -x.y;
+        return c_scale(x, in ? w : 0.f);
+      };
+      team_pass1<LOGM, +1>(tt, buf, load);
+    }
+    __syncwarp();  // a team lies inside one warp
+    if (active) {
+      float2 res[T::HELD];
+      team_pass2<LOGM, +1>(tt, buf, [&](int j, int r) { return c_conj(s_tw[r * T::R1 + j]); }, res);
+      float2* out = a.coef + s * a.cps + bd.coef_off;
+#pragma unroll
+      for (int i = 0; i < T::J2; ++i)
+#pragma unroll
+        for (int r = 0; r < T::R2; ++r) __stcs(out + team_out_index<LOGM>(tt, i, r), res[i * T::R2 + r]);
+    }
+    __syncthreads();  // the footprint buffer is refilled two slices later
+  }
+  cp_async_wait<0>();
+}
+
+__global__ void __launch_bounds__(kBandThreads, 1) band_analysis_persistent_kernel(
+    BandArgs a, const int2* __restrict__ cta_map, const int* __restrict__ lanes_of) {
+  extern __shared__ float2 sm[];
+  const int2 gl = cta_map[blockIdx.x];  // (group, lane)
+  const GroupDesc gd = a.groups[gl.x];
+  const int lanes = lanes_of[gl.x];
+  const int64_t total = a.total;
+  switch (gd.log2M) {
+    case 4: analysis_persistent<4>(a, gd, gl.y, lanes, total, sm); break;
+    case 5: analysis_persistent<5>(a, gd, gl.y, lanes, total, sm); break;
+    case 6: analysis_persistent<6>(a, gd, gl.y, lanes, total, sm); break;
+    case 7: analysis_persistent<7>(a, gd, gl.y, lanes, total, sm); break;
+    case 8: analysis_persistent<8>(a, gd, gl.y, lanes, total, sm); break;
+    case 9: analysis_persistent<9>(a, gd, gl.y, lanes, total, sm); break;
+    case 10: analysis_persistent<10>(a, gd, gl.y, lanes, total, sm); break;
+  }
+}
+
 // ----------------------------------------------------------- synthesis ---
 
 // Per-channel fields the gather needs, staged in shared memory.
@@ -178,6 +280,7 @@ __device__ __forceinline__ void synthesis_weight(const BandArgs& a, const BandDe
 // channels from the highest covering one down, then the mirrored channels.
 __device__ __forceinline__ float2 gather_bin(int h, int& last, int nb, const GatherBand* gb,
                                              const GroupDesc& gd, const BandDesc* __restrict__ bands,
+                                             const int32_t* __restrict__ mirror_list,
                                              const float2* sm, int twoN) {
   while (last + 1 < nb && gb[last + 1].dlo <= h) ++last;
   float2 acc = make_float2(0.f, 0.f);
@@ -190,7 +293,7 @@ __device__ __forceinline__ float2 gather_bin(int h, int& last, int nb, const Gat
     acc = c_add(acc, sm[b.base + o]);
   }
   for (int i = 0; i < gd.nmirror; ++i) {
-    const BandDesc bd = bands[gd.mirror[i]];
+    const BandDesc bd = bands[mirror_list[gd.mirror_off + i]];
     if (h < bd.mlo || h > bd.mhi) continue;
     const int bm = h == 0 ? 0 : twoN - h;
     int o = bm - bd.j0;
@@ -287,7 +390,7 @@ __global__ void __launch_bounds__(kBandThreads) band_synthesis_kernel(BandArgs a
       last = s_gb[lo].dlo <= h ? lo : -1;
     }
     for (; h < gd.acc_hi; h += blockDim.x) {
-      const float2 v = gather_bin(h, last, nb, s_gb, gd, a.bands, sm, twoN);
+      const float2 v = gather_bin(h, last, nb, s_gb, gd, a.bands, a.mirror_list, sm, twoN);
       if (h < bl_hi) patch_l[h] = v;
       else if (h >= br_lo) patch_r[h] = v;
       else spec[h] = v;
@@ -325,6 +428,7 @@ BandArgs make_args(const slicq_plan* pl, const Workspace& ws, const float* win) 
   a.groups = pl->d_groups;
   a.bounds = pl->d_bounds;
   a.thread_band = pl->d_thread_band;
+  a.mirror_list = pl->d_mirror_list;
   a.win = win;
   a.twband = pl->d_twband;
   a.spec = ws.spec;
@@ -344,17 +448,13 @@ cudaError_t launch_band_analysis(const slicq_plan* pl, const Workspace& ws, int6
                                  float2* coef, cudaStream_t st) {
   BandArgs a = make_args(pl, ws, pl->d_ga);
   a.coef = coef;
-  cudaError_t e = cudaFuncSetAttribute(band_analysis_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, pl->band_smem_a);
+  a.total = batch * ws.S;
+  cudaError_t e = cudaFuncSetAttribute(band_analysis_persistent_kernel,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, pl->band_smem_p);
   if (e != cudaSuccess) return e;
-  const int64_t total = batch * ws.S;
-  for (int64_t s0 = 0; s0 < total; s0 += kMaxGridY) {
-    a.slice_base = s0;
-    dim3 grid(pl->G, (unsigned)(total - s0 < kMaxGridY ? total - s0 : kMaxGridY));
-    band_analysis_kernel<<<grid, kBandThreads, pl->band_smem_a, st>>>(a);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  band_analysis_persistent_kernel<<<pl->n_cta_a, kBandThreads, pl->band_smem_p, st>>>(
+      a, pl->d_cta_map, pl->d_lanes);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_band_synthesis(const slicq_plan* pl, const float2* coef, int64_t batch,

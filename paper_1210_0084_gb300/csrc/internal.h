@@ -40,7 +40,7 @@ struct GroupDesc {
   int32_t ex_lo, ex_hi;          // bins only this group touches
   int32_t left_bd, right_bd;     // boundary indices, -1 if none
   int32_t nmirror;               // channels of the group with mirrored bins
-  int32_t mirror[16];            // their indices
+  int32_t mirror_off;            // their indices: mirror_list[mirror_off ..]
   int32_t log2M;                 // every channel of the group has M = 2^log2M
   int32_t fp_lo, fp_len;         // spectrum block the analysis stages (even bounds)
   int32_t pad_;
@@ -49,6 +49,15 @@ struct GroupDesc {
 // Bins [lo, hi) touched by two neighbouring groups (bd and bd + 1).
 struct BoundaryDesc {
   int32_t lo, hi;
+};
+
+// One slice row of a ragged batch: the clip it belongs to and where that
+// clip's samples are (uniform batches compute the same from (row / S)).
+struct RowDesc {
+  int64_t sig_off;   // first sample of the clip in the signal buffer
+  int32_t n, L;      // clip length, padded length (multiple of 2N)
+  int32_t S, m;      // slices of the clip, this row's slice index
+  int64_t tr_base;   // overlap-add slot of the clip's transition 0
 };
 
 // Which of the plan's window tables a synthesis launch uses.
@@ -72,6 +81,9 @@ struct slicq_plan {
   int band_in_a = 0;      // complex values per staged analysis input (max footprint)
   int band_in_s = 0;      // complex values per staged synthesis input (max group block)
   int num_sms = 152;      // SMs of the plan's device (grid sizing)
+  int band_smem_p = 0;    // dynamic shared memory of the persistent band analysis (bytes)
+  int n_cta_a = 0;        // CTAs of the persistent band analysis
+  std::vector<int> group_cost;  // relative work of one slice of each group
   int slice_smem = 0;     // dynamic shared memory of the slice kernels (bytes)
   int slice_tw_off = 0;   // float2 offset of the twiddle tables in that memory
   int tw_lb = 0;          // log2 of the fine twiddle table length
@@ -81,6 +93,7 @@ struct slicq_plan {
   std::vector<slicq::GroupDesc> groups;
   std::vector<slicq::BoundaryDesc> bounds;
   std::vector<int16_t> thread_band;  // [G][kBandThreads] channel or -1
+  std::vector<int32_t> mirror_list;  // channels with mirrored bins, grouped by group
   std::vector<double> xi, omega;     // Table 1, channels 0..K+1
   std::vector<int64_t> jlo;          // unwrapped first support sample
 
@@ -90,10 +103,14 @@ struct slicq_plan {
   slicq::GroupDesc* d_groups = nullptr;
   slicq::BoundaryDesc* d_bounds = nullptr;
   int16_t* d_thread_band = nullptr;
+  int32_t* d_mirror_list = nullptr;
   float* d_ga = nullptr;    // g_k / sqrt(2N)
   float* d_gs = nullptr;    // w_k g~_k / sqrt(2N)
   float* d_gadj = nullptr;  // g_k / (2 sqrt(2N))
   float* d_hw = nullptr;    // Tukey transition, M + 1 values
+  float* d_h0 = nullptr;    // h_0 over one slice, 2N values
+  int2* d_cta_map = nullptr;  // persistent band analysis: CTA -> (group, lane)
+  int* d_lanes = nullptr;     // lanes (CTAs) per group
   float2* d_tw_lo = nullptr;  // exp(-2 pi i t / 2N), t < 2^tw_lb
   float2* d_tw_hi = nullptr;  // exp(-2 pi i (t << tw_lb) / 2N)
   float2* d_twband = nullptr; // band pass-2 twiddles, per length, [r][j] layout
@@ -114,6 +131,9 @@ namespace slicq {
 // Host layout (no device): fills everything in `pl` above the arena.
 slicq_status build_layout(const slicq_params* p, slicq_plan* pl);
 
+// Workspace partition for `rows` slice rows of a ragged batch (S = rows, L unused).
+size_t workspace_layout_rows(const slicq_plan* pl, int64_t rows, void* base, struct Workspace* ws);
+
 // Workspace partition for (n_samples, batch).
 struct Workspace {
   int64_t S = 0, L = 0;
@@ -132,7 +152,7 @@ size_t workspace_layout(const slicq_plan* pl, int64_t n_samples, int64_t batch,
 // Kernel launchers (return cudaGetLastError() of the launch).
 cudaError_t launch_slice_forward(const slicq_plan* pl, const float* f,
                                  int64_t n, int64_t batch, const Workspace& ws,
-                                 cudaStream_t st);
+                                 cudaStream_t st, const RowDesc* rows = nullptr);
 cudaError_t launch_band_analysis(const slicq_plan* pl, const Workspace& ws,
                                  int64_t batch, float2* coef, cudaStream_t st);
 cudaError_t launch_band_synthesis(const slicq_plan* pl, const float2* coef,
@@ -141,6 +161,6 @@ cudaError_t launch_band_synthesis(const slicq_plan* pl, const float2* coef,
 cudaError_t launch_slice_inverse(const slicq_plan* pl, int64_t n,
                                  int64_t batch, SynthKind kind,
                                  const Workspace& ws, float* out,
-                                 cudaStream_t st);
+                                 cudaStream_t st, const RowDesc* rows = nullptr);
 
 }  // namespace slicq

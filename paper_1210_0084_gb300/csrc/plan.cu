@@ -143,7 +143,9 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
   // ---- band groups: consecutive channels, <= kBandThreads threads each
   pl->groups.clear();
   pl->thread_band.clear();
-  int in_a = 0, in_s = 0, tb_max = 0;  // complex values
+  pl->mirror_list.clear();
+  int in_a = 0, in_s = 0, tb_max = 0, smem_p = 0;  // complex values
+  pl->group_cost.clear();
   {
     int k = 0;
     while (k < nch) {
@@ -182,8 +184,9 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
           prev_dhi = d.dhi;
         }
         if (d.mhi >= 0) {
-          if (gd.nmirror == 16) return SLICQ_EUNSUPPORTED;
-          gd.mirror[gd.nmirror++] = b;
+          if (gd.nmirror == 0) gd.mirror_off = (int)pl->mirror_list.size();
+          pl->mirror_list.push_back(b);
+          ++gd.nmirror;
         }
       }
       if (ahi < 0) return SLICQ_EINVAL;
@@ -199,6 +202,8 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
         in_a = std::max(in_a, gd.fp_len);
         in_s = std::max(in_s, nb * M);
         tb_max = std::max(tb_max, nb * bufl);
+        smem_p = std::max(smem_p, M + 2 * gd.fp_len + nb * bufl);
+        pl->group_cost.push_back(nb * M * (gd.log2M + 4));
       }
       (void)smem;
       pl->groups.push_back(gd);
@@ -251,6 +256,8 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
   // per-slice band kernels: one team buffer per channel of the group
   pl->band_smem_a = tb_max * (int)sizeof(float2);
   pl->band_smem_s = tb_max * (int)sizeof(float2);
+  pl->band_smem_p = smem_p * (int)sizeof(float2);
+  if (pl->band_smem_p > 220 * 1024) return SLICQ_EUNSUPPORTED;
   if (pl->band_smem_a > 220 * 1024 || pl->band_smem_s > 220 * 1024) return SLICQ_EUNSUPPORTED;
 
   // ---- slice FFT geometry: N = P Q, cluster of C CTAs, <= 256 threads each
@@ -395,6 +402,22 @@ __global__ void k_twiddles(int64_t L2, int lb, int logQ, float2* lo, float2* hi,
   }
 }
 
+// h_0 over a whole slice, j = 0..2N-1 (the slice kernel's input weights)
+__global__ void k_slice_window(int64_t N, int64_t M, float* h0) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= 2 * N) return;
+  const int64_t d = j > N ? j - N : N - j;
+  const int64_t a0 = (N - M) / 2;
+  double v = 0.0;
+  if (d <= a0) {
+    v = 1.0;
+  } else if (2 * d < N + M) {
+    const double c = cospi(0.5 * (double)(d - a0) / (double)M);
+    v = c * c;
+  }
+  h0[j] = (float)v;
+}
+
 // Tukey transition h_0 at |j - N| = (N - M)/2 + o, o = 0..M
 __global__ void k_tukey(int64_t M, float* hw) {
   const int64_t o = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -418,10 +441,30 @@ slicq_status build_tables(slicq_plan* pl) {
   const size_t o_groups = take(sizeof(GroupDesc) * pl->G);
   const size_t o_bounds = take(sizeof(BoundaryDesc) * pl->bounds.size());
   const size_t o_tb = take(sizeof(int16_t) * pl->thread_band.size());
+  const size_t o_ml = take(sizeof(int32_t) * std::max<size_t>(pl->mirror_list.size(), 1));
   const size_t o_ga = take(sizeof(float) * (pl->win_total + 32));  // + padding
   const size_t o_gs = take(sizeof(float) * (pl->win_total + 32));  // + padding
   const size_t o_gadj = take(sizeof(float) * (pl->win_total + 32));  // + padding
+  // persistent band analysis: the same number of lanes (CTAs) per group, one
+  // CTA per SM in total (at least one per group).  A slice of any group costs
+  // a similar fixed part (staging, barriers) plus its transforms; equal lanes
+  // measured faster than lanes proportional to the transform work.
+  std::vector<int> lanes(pl->G, 1);
+  {
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl->device) == cudaSuccess && sms > 0)
+      pl->num_sms = sms;
+    const int per = std::max(1, pl->num_sms / pl->G);
+    for (int g = 0; g < pl->G; ++g) lanes[g] = per;
+    pl->n_cta_a = per * pl->G;
+  }
+  std::vector<int2> cta_map;
+  for (int g = 0; g < pl->G; ++g)
+    for (int y = 0; y < lanes[g]; ++y) cta_map.push_back(make_int2(g, y));
+  const size_t o_map = take(sizeof(int2) * cta_map.size());
+  const size_t o_lanes = take(sizeof(int) * pl->G);
   const size_t o_hw = take(sizeof(float) * (Mtr + 1));
+  const size_t o_h0 = take(sizeof(float) * L2);
   const size_t o_twlo = take(sizeof(float2) * (size_t(1) << pl->tw_lb));
   const size_t o_twhi = take(sizeof(float2) * (L2 >> pl->tw_lb));
   const size_t o_twband = take(sizeof(float2) * 2032);
@@ -432,10 +475,14 @@ slicq_status build_tables(slicq_plan* pl) {
   pl->d_groups = (GroupDesc*)(base + o_groups);
   pl->d_bounds = (BoundaryDesc*)(base + o_bounds);
   pl->d_thread_band = (int16_t*)(base + o_tb);
+  pl->d_mirror_list = (int32_t*)(base + o_ml);
   pl->d_ga = (float*)(base + o_ga);
   pl->d_gs = (float*)(base + o_gs);
   pl->d_gadj = (float*)(base + o_gadj);
   pl->d_hw = (float*)(base + o_hw);
+  pl->d_h0 = (float*)(base + o_h0);
+  pl->d_cta_map = (int2*)(base + o_map);
+  pl->d_lanes = (int*)(base + o_lanes);
   pl->d_tw_lo = (float2*)(base + o_twlo);
   pl->d_tw_hi = (float2*)(base + o_twhi);
   pl->d_twband = (float2*)(base + o_twband);
@@ -457,6 +504,13 @@ slicq_status build_tables(slicq_plan* pl) {
   if (e == cudaSuccess)
     e = cudaMemcpy(pl->d_thread_band, pl->thread_band.data(),
                    sizeof(int16_t) * pl->thread_band.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !pl->mirror_list.empty())
+    e = cudaMemcpy(pl->d_mirror_list, pl->mirror_list.data(), sizeof(int32_t) * pl->mirror_list.size(),
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(pl->d_cta_map, cta_map.data(), sizeof(int2) * cta_map.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(pl->d_lanes, lanes.data(), sizeof(int) * pl->G, cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return SLICQ_ECUDA;
 
   // temporaries for the FP64 computation
@@ -506,6 +560,10 @@ slicq_status build_tables(slicq_plan* pl) {
     }
     if (e == cudaSuccess) {
       k_tukey<<<(unsigned)((Mtr + 1 + T - 1) / T), T>>>(Mtr, pl->d_hw);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+      k_slice_window<<<(unsigned)((L2 + T - 1) / T), T>>>(pl->N, Mtr, pl->d_h0);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) e = cudaDeviceSynchronize();

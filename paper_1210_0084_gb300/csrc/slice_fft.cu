@@ -39,12 +39,14 @@ struct SliceArgs {
   int S, N, Mtr;
   int C, logQc, logPc;
   const float* __restrict__ hw;   // Tukey transition, Mtr + 1 values
+  const float2* __restrict__ h0;  // h_0 over the slice as pairs (h_0[2e], h_0[2e+1])
   TwiddleTables tw;               // global two-level tables (copied to shared memory)
   const float2* __restrict__ tw4; // four-step twiddles exp(-2 pi i q u / N) at [u Q + q]
   int tw_off;                     // shared-memory offset (float2) of the table copy
   float* ola_patch;               // [slice][2][Mtr]
   uint32_t* ola_cnt;              // [slice][C]
   unsigned long long* items;      // band-kernel work counter this launch resets
+  const RowDesc* __restrict__ rows;  // ragged batch: per-row clip description (or null)
   int adjoint;                    // multiply the output by h_0 instead of 1
 };
 
@@ -54,6 +56,24 @@ __device__ __forceinline__ float slicing_window(const SliceArgs& a, int j) {
   const int a0 = (a.N - a.Mtr) >> 1;
   const float ht = __ldg(a.hw + min(max(d - a0, 0), a.Mtr));
   return d <= a0 ? 1.f : (2 * d < a.N + a.Mtr ? ht : 0.f);
+}
+
+// Clip of slice row s: signal offset, length, padded length, slice index.
+__device__ __forceinline__ void row_of(const SliceArgs& a, int64_t s, int64_t& sig_off, int& n,
+                                       int& L, int& m) {
+  if (a.rows) {
+    const RowDesc r = a.rows[s];
+    sig_off = r.sig_off;
+    n = r.n;
+    L = r.L;
+    m = r.m;
+  } else {
+    const int64_t b = s / a.S;
+    sig_off = b * a.n;
+    n = (int)a.n;
+    L = (int)a.L;
+    m = (int)(s - b * a.S);
+  }
 }
 
 template <int LOGP, int LOGQ>
@@ -169,25 +189,26 @@ __device__ __forceinline__ void fourstep(const SliceArgs& a, cg::cluster_group& 
 // ------------------------------------------------------------- forward ---
 
 template <int LOGP, int LOGQ>
-__global__ void __launch_bounds__(kSliceMaxThreads, 2) slice_forward_kernel(SliceArgs a) {
+__global__ void __launch_bounds__(kSliceMaxThreads) slice_forward_kernel(SliceArgs a) {
   using G = Geo<LOGP, LOGQ>;
   using TQ = typename G::TQ;
   extern __shared__ float2 sm[];
   cg::cluster_group cluster = cg::this_cluster();
   const int64_t s = blockIdx.x / a.C;
-  const int64_t b = s / a.S;
-  const int m = (int)(s - b * a.S);
-  const float* f = a.f + b * a.n;
-  const int n32 = (int)a.n, L32 = (int)a.L;   // the entry points keep L < 2^31
+  int64_t sig_off;
+  int n32, L32, m;                            // the entry points keep L < 2^31
+  row_of(a, s, sig_off, n32, L32, m);
+  const float* f = a.f + sig_off;
   const int base = (m - 1) * a.N;             // position of slice sample 0 (slice 0: -N)
-  const bool vec = ((b * a.n) & 1) == 0;      // f is 8-byte aligned (uniform per CTA)
+  const bool vec = (sig_off & 1) == 0;        // f is 8-byte aligned (uniform per CTA)
 
   // Element e of the packed slice is (x[2e], x[2e+1]); x[j] = f[j + (m-1)N] h_0[j-N].
   // Branch-free: every load is issued with a clamped index and weighted by 0
   // outside the support of h_0 and past the end of the signal.
   auto load = [&](int e) -> float2 {
     const int j = 2 * e;
-    const float w0 = slicing_window(a, j), w1 = slicing_window(a, j + 1);
+    const float2 w = __ldg(a.h0 + e);
+    const float w0 = w.x, w1 = w.y;
     int t = base + j;
     if (t < 0) t += L32; else if (t >= L32) t -= L32;   // t even, t + 1 < L
     const bool in0 = t < n32, in1 = t + 1 < n32;
@@ -254,7 +275,7 @@ __global__ void __launch_bounds__(kSliceMaxThreads, 2) slice_forward_kernel(Slic
 // this CTA holds.
 template <class Each>
 __device__ __forceinline__ void ola_combine(const SliceArgs& a, int64_t tr_slot, int side,
-                                            int rank, int* s_flag, float* out, Each each) {
+                                            int rank, int* s_flag, float* out, int n32, Each each) {
   float* mine = a.ola_patch + (tr_slot * 2 + side) * (int64_t)a.Mtr;
   const float* other = a.ola_patch + (tr_slot * 2 + (1 - side)) * (int64_t)a.Mtr;
   each([&](int o, int tpos, float v) { mine[o] = v; });
@@ -268,7 +289,7 @@ __device__ __forceinline__ void ola_combine(const SliceArgs& a, int64_t tr_slot,
   if (*s_flag) {
     __threadfence();
     each([&](int o, int tpos, float v) {
-      if (tpos < a.n) out[tpos] = v + __ldcg(other + o);
+      if (tpos < n32) out[tpos] = v + __ldcg(other + o);
     });
   }
   __syncthreads();
@@ -282,8 +303,11 @@ __global__ void __launch_bounds__(kSliceMaxThreads) slice_inverse_kernel(SliceAr
   __shared__ int s_flag;
   cg::cluster_group cluster = cg::this_cluster();
   const int64_t s = blockIdx.x / a.C;
-  const int64_t b = s / a.S;
-  const int m = (int)(s - b * a.S);
+  int64_t sig_off;
+  int n32, L32, m;
+  row_of(a, s, sig_off, n32, L32, m);
+  const int Sc = L32 / a.N;                   // slices of this row's clip
+  const int64_t tr0 = a.rows ? a.rows[s].tr_base : s - m;  // slot of the clip's transition 0
   const float2* H = a.spec + s * a.spec_stride;
   const int N = a.N;
 
@@ -320,9 +344,8 @@ __global__ void __launch_bounds__(kSliceMaxThreads) slice_inverse_kernel(SliceAr
   const int Pc = 1 << a.logPc;
   const int rank = (int)cluster.block_rank();
   const int a0 = (N - a.Mtr) >> 1;
-  const int n32 = (int)a.n, L32 = (int)a.L;
   const int base = (m - 1) * N;
-  float* out = a.out + b * a.n;
+  float* out = a.out + sig_off;
   auto tpos_of = [&](int j) -> int {
     int t = base + j;
     if (t < 0) t += L32; else if (t >= L32) t -= L32;
@@ -379,9 +402,8 @@ __global__ void __launch_bounds__(kSliceMaxThreads) slice_inverse_kernel(SliceAr
       }
     });
   };
-  const int64_t bS = b * a.S;
-  ola_combine(a, bS + m, 0, rank, &s_flag, out, each_right);
-  ola_combine(a, bS + (m + a.S - 1) % a.S, 1, rank, &s_flag, out, each_left);
+  ola_combine(a, tr0 + m, 0, rank, &s_flag, out, n32, each_right);
+  ola_combine(a, tr0 + (m + Sc - 1) % Sc, 1, rank, &s_flag, out, n32, each_left);
   // no remote shared-memory access after the exchange inside fourstep()
 }
 
@@ -436,6 +458,7 @@ SliceArgs make_args(const slicq_plan* pl, const Workspace& ws, int64_t n) {
   a.logQc = pl->logQ - ilog2c(pl->C);
   a.logPc = pl->logP - ilog2c(pl->C);
   a.hw = pl->d_hw;
+  a.h0 = reinterpret_cast<const float2*>(pl->d_h0);
   a.tw = TwiddleTables{pl->d_tw_lo, pl->d_tw_hi, pl->tw_lb};
   a.tw_off = pl->slice_tw_off;
   a.tw4 = pl->d_tw4;
@@ -447,18 +470,20 @@ SliceArgs make_args(const slicq_plan* pl, const Workspace& ws, int64_t n) {
 }  // namespace
 
 cudaError_t launch_slice_forward(const slicq_plan* pl, const float* f, int64_t n, int64_t batch,
-                                 const Workspace& ws, cudaStream_t st) {
+                                 const Workspace& ws, cudaStream_t st, const RowDesc* rows) {
   SliceArgs a = make_args(pl, ws, n);
   a.f = f;
   a.items = ws.items + 0;
+  a.rows = rows;
   return dispatch(true, pl, a, batch * ws.S, st);
 }
 
 cudaError_t launch_slice_inverse(const slicq_plan* pl, int64_t n, int64_t batch, SynthKind kind,
-                                 const Workspace& ws, float* out, cudaStream_t st) {
+                                 const Workspace& ws, float* out, cudaStream_t st, const RowDesc* rows) {
   SliceArgs a = make_args(pl, ws, n);
   a.out = out;
   a.items = ws.items + 1;
+  a.rows = rows;
   a.adjoint = kind == kSynthAdjoint;
   return dispatch(false, pl, a, batch * ws.S, st);
 }

@@ -28,7 +28,7 @@ import numpy as np
 
 __all__ = [
     "SliCQParams", "SliCQPlan", "SliCQError", "SliCQFunction", "slicq_transform",
-    "layout", "lib_path", "load_library", "STATUS",
+    "layout", "lib_path", "load_library", "STATUS", "SliCQBatch",
 ]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -84,6 +84,12 @@ def load_library():
         "slicq_adjoint": (ctypes.c_int, [VP, VP, I64, I64, VP, VP, SZ, VP]),
         "slicq_plan_table": (ctypes.c_int, [VP, I32, VP, I64, ctypes.POINTER(I64)]),
         "slicq_trace_enable": (ctypes.c_int, [VP, I32]),
+        "slicq_batch_create": (ctypes.c_int, [VP, I32, VP, VP, I32, ctypes.POINTER(VP)]),
+        "slicq_batch_destroy": (None, [VP]),
+        "slicq_batch_layout": (ctypes.c_int, [VP, VP, VP, VP, ctypes.POINTER(I64), ctypes.POINTER(I64),
+                                              ctypes.POINTER(SZ)]),
+        "slicq_batch_forward": (ctypes.c_int, [VP, VP, VP, VP, SZ, VP]),
+        "slicq_batch_inverse": (ctypes.c_int, [VP, VP, VP, VP, SZ, VP]),
         "slicq_trace_read": (ctypes.c_int, [VP, VP, VP, I32, ctypes.POINTER(I32)]),
     }
     for name, (res, args) in sig.items():
@@ -306,3 +312,80 @@ def SliCQFunction():
 def slicq_transform(x, plan: SliCQPlan):
     """Differentiable forward sliCQ of a float32 CUDA tensor [batch, n]."""
     return SliCQFunction().apply(x, plan)
+
+
+class SliCQBatch:
+    """A ragged batch: clips of different lengths over several plans of one
+    slice geometry, transformed in one call (plans as concurrent branches)."""
+
+    def __init__(self, plans, clip_plan, clip_samples):
+        import torch
+        self._torch = torch
+        self.plans = list(plans)
+        self.lib = load_library()
+        self.device = self.plans[0].device
+        n = len(clip_plan)
+        self.n_clips = n
+        self.clip_plan = np.asarray(clip_plan, np.int32)
+        self.clip_samples = np.asarray(clip_samples, np.int64)
+        arr = (ctypes.c_void_p * len(self.plans))(*[p.handle.value for p in self.plans])
+        h = ctypes.c_void_p()
+        _check(self.lib.slicq_batch_create(arr, len(self.plans), self.clip_plan.ctypes.data,
+                                           self.clip_samples.ctypes.data, n, ctypes.byref(h)),
+               "slicq_batch_create")
+        self._h = h
+        self.sig_off = np.zeros(n, np.int64)
+        self.coef_off = np.zeros(n, np.int64)
+        self.slices = np.zeros(n, np.int64)
+        st, ct = ctypes.c_int64(), ctypes.c_int64()
+        wb = ctypes.c_size_t()
+        _check(self.lib.slicq_batch_layout(h, self.sig_off.ctypes.data, self.coef_off.ctypes.data,
+                                           self.slices.ctypes.data, ctypes.byref(st), ctypes.byref(ct),
+                                           ctypes.byref(wb)), "slicq_batch_layout")
+        self.sig_total, self.coef_total, self.work_bytes = st.value, ct.value, wb.value
+        self.work = torch.zeros(max(self.work_bytes, 256), dtype=torch.uint8, device=f"cuda:{self.device}")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            try:
+                self.lib.slicq_batch_destroy(h)
+            except Exception:
+                pass
+            self._h = None
+
+    def pack(self, signals):
+        """Concatenate per-clip float32 arrays into the batch's signal layout."""
+        t = self._torch
+        buf = t.zeros(self.sig_total, dtype=t.float32, device=f"cuda:{self.device}")
+        for c, x in enumerate(signals):
+            xt = t.as_tensor(np.asarray(x, np.float32)).to(buf.device)
+            buf[self.sig_off[c]: self.sig_off[c] + self.clip_samples[c]] = xt
+        return buf
+
+    def clip_signal(self, sig, c):
+        return sig[self.sig_off[c]: self.sig_off[c] + self.clip_samples[c]]
+
+    def clip_coefs(self, coef, c):
+        cps = self.plans[self.clip_plan[c]].coefs_per_slice
+        o = int(self.coef_off[c])
+        return coef[o: o + int(self.slices[c]) * cps].view(int(self.slices[c]), cps)
+
+    def _stream(self):
+        return ctypes.c_void_p(self._torch.cuda.current_stream(self.device).cuda_stream)
+
+    def forward(self, sig, out=None):
+        t = self._torch
+        if out is None:
+            out = t.empty(self.coef_total, dtype=t.complex64, device=sig.device)
+        _check(self.lib.slicq_batch_forward(self._h, sig.data_ptr(), out.data_ptr(), self.work.data_ptr(),
+                                            self.work.numel(), self._stream()), "slicq_batch_forward")
+        return out
+
+    def inverse(self, coef, out=None):
+        t = self._torch
+        if out is None:
+            out = t.zeros(self.sig_total, dtype=t.float32, device=coef.device)
+        _check(self.lib.slicq_batch_inverse(self._h, coef.data_ptr(), out.data_ptr(), self.work.data_ptr(),
+                                            self.work.numel(), self._stream()), "slicq_batch_inverse")
+        return out

@@ -60,6 +60,7 @@ SMALL = [
     (44100.0, 32.7, 22050.0, 48, 65536, 16384, 150000, 1), # bench plan, cluster of 4
     (16000.0, 50.0, 8000.0, 24, 2048, 512, 1500, 1),       # n < 2N: two slices
     (44100.0, 40.0, 22050.0, 48, 8192, 2048, 30000, 2),    # several channels cross DC
+    (48000.0, 50.0, 22000.0, 96, 4096, 1024, 20000, 1),    # ~90 widened channels cross DC
 ]
 
 
