@@ -34,6 +34,7 @@ struct BandArgs {
   const int32_t* __restrict__ mirror_list;  // channels with mirrored bins, per group
   const float* __restrict__ win;     // window table of this launch
   const float2* __restrict__ twband; // pass-2 twiddle tables, kTwSmall entries
+  const float2* __restrict__ tw4096; // exp(-2 pi i t / 4096), t < 4096 (three-pass lengths)
   float2* spec;                      // [slice][spec_stride]
   int64_t slice_base;                // first slice of this launch (per-slice kernels)
   int64_t total;                     // slices of the call (persistent kernel)
@@ -60,86 +61,6 @@ struct BandTw {
   }
 };
 
-// ------------------------------------------------------------ analysis ---
-
-template <int LOGM>
-__device__ __forceinline__ void analysis_pass1(const BandArgs& a, const BandDesc& bd, int tt,
-                                               const float2* __restrict__ X, float2* buf) {
-  constexpr int M = 1 << LOGM;
-  const int twoN = 2 * a.N;
-  const float* __restrict__ g = a.win + bd.win_off;
-  // branch-free: every load is issued, out-of-support residues get weight 0
-  // (the window table has padding after its last channel)
-  auto load = [&](int idx) -> float2 {
-    const int o = (idx - bd.j0) & (M - 1);
-    const bool in = o < bd.len;
-    const int oc = in ? o : 0;
-    int b = bd.j0 + oc;
-    if (b >= twoN) b -= twoN;
-    const bool mir = b > a.N;
-    float2 x = X[mir ? twoN - b : b];
-    const float w = __ldg(g + oc);
-    if (mir) x.y = -x.y;
-    return c_scale(x, in ? w : 0.f);
-  };
-  team_pass1<LOGM, +1>(tt, buf, load);
-}
-
-template <int LOGM>
-__device__ __forceinline__ void analysis_pass2(int tt, const float2* buf, const float2* s_tw,
-                                               float2* __restrict__ out) {
-  using T = Team<LOGM>;
-  float2 res[T::HELD];
-  team_pass2<LOGM, +1>(tt, buf, BandTw<LOGM, +1>{s_tw}, res);
-#pragma unroll
-  for (int i = 0; i < T::J2; ++i)
-#pragma unroll
-    for (int r = 0; r < T::R2; ++r)
-      __stcs(out + team_out_index<LOGM>(tt, i, r), res[i * T::R2 + r]);
-}
-
-__global__ void __launch_bounds__(kBandThreads) band_analysis_kernel(BandArgs a) {
-  extern __shared__ float2 sm[];
-  __shared__ float2 s_tw[kTwSmall];
-  const int g = blockIdx.x;
-  const int64_t s = a.slice_base + blockIdx.y;
-  const int t = threadIdx.x;
-  const int k = a.thread_band[g * kBandThreads + t];
-  BandDesc bd{};
-  if (k >= 0) bd = a.bands[k];
-  const int tt = t - bd.tofs;
-  const float2* X = a.spec + s * a.spec_stride;
-  float2* buf = sm + bd.smem_off;
-  load_twiddles(a, s_tw);
-  __syncthreads();  // the table is filled by all threads; the passes only sync per warp
-  if (k >= 0) {
-    switch (bd.log2M) {
-      case 4: analysis_pass1<4>(a, bd, tt, X, buf); break;
-      case 5: analysis_pass1<5>(a, bd, tt, X, buf); break;
-      case 6: analysis_pass1<6>(a, bd, tt, X, buf); break;
-      case 7: analysis_pass1<7>(a, bd, tt, X, buf); break;
-      case 8: analysis_pass1<8>(a, bd, tt, X, buf); break;
-      case 9: analysis_pass1<9>(a, bd, tt, X, buf); break;
-      case 10: analysis_pass1<10>(a, bd, tt, X, buf); break;
-    }
-  }
-  // a team (one channel) lies inside one warp: the groups hold channels of
-  // one length and teams start at multiples of their size
-  __syncwarp();
-  if (k >= 0) {
-    float2* out = a.coef + s * a.cps + bd.coef_off;
-    switch (bd.log2M) {
-      case 4: analysis_pass2<4>(tt, buf, s_tw, out); break;
-      case 5: analysis_pass2<5>(tt, buf, s_tw, out); break;
-      case 6: analysis_pass2<6>(tt, buf, s_tw, out); break;
-      case 7: analysis_pass2<7>(tt, buf, s_tw, out); break;
-      case 8: analysis_pass2<8>(tt, buf, s_tw, out); break;
-      case 9: analysis_pass2<9>(tt, buf, s_tw, out); break;
-      case 10: analysis_pass2<10>(tt, buf, s_tw, out); break;
-    }
-  }
-}
-
 // --------------------------------------------------------------- cp.async ---
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
@@ -159,24 +80,68 @@ __device__ __forceinline__ void cp_async_wait() {
 // current one is transformed.  Shared memory: [twiddles M][footprint x 2]
 // [team buffers].
 
+// exp(SIGN 2 pi i e / n) for n | 4096, from the global W_4096 table (L1-resident)
+template <int SIGN>
+struct Tw4096 {
+  const float2* __restrict__ t;
+  __device__ __forceinline__ float2 operator()(int e, int n) const {
+    const float2 w = __ldg(t + e * (4096 / n));
+    return SIGN < 0 ? w : c_conj(w);
+  }
+};
+
+// Three-pass transform of one band of length 2^LOGM (2048, 4096) by its team
+// (several warps).  Every thread of the CTA calls this (the group holds
+// channels of one length); threads without a channel only join the barriers.
+// IN(idx) gives input element idx; OUT(idx, v) takes the result element idx
+// (its writes may overwrite `buf`: a barrier separates them from the reads).
+template <int LOGM, int SIGN, class In, class Out>
+__device__ __forceinline__ void band_three_pass(bool active, int tt, float2* buf, const float2* tw4096,
+                                                In in, Out out) {
+  using T = Team3<LOGM>;
+  constexpr int L = T::L;
+  const Tw4096<SIGN> tw{tw4096};
+  auto nosync = [] {};
+  auto cta = [] { __syncthreads(); };
+  if (active)
+    stockham_pass<L, T::R0, 1, SIGN, T::TT>(tt, in, tw, nosync, [&](int i, float2 v) { buf[i] = v; });
+  __syncthreads();
+  if (active) {
+    stockham_pass<L, T::R1, T::R0, SIGN, T::TT>(tt, [&](int i) { return buf[i]; }, tw, cta,
+                                                [&](int i, float2 v) { buf[i] = v; });
+  } else {
+    __syncthreads();
+  }
+  __syncthreads();
+  if (active) {
+    stockham_pass<L, T::R2, T::R0 * T::R1, SIGN, T::TT>(tt, [&](int i) { return buf[i]; }, tw, cta, out);
+  } else {
+    __syncthreads();
+  }
+}
+
 template <int LOGM>
 __device__ void analysis_persistent(const BandArgs& a, const GroupDesc& gd, int lane, int lanes,
                                     int64_t total, float2* sm) {
-  using T = Team<LOGM>;
+  constexpr bool THREE = LOGM > kMaxTwoPassLog2;
+  using T = Team<THREE ? 10 : LOGM>;
   constexpr int M = 1 << LOGM;
+  constexpr int TT = THREE ? Team3<THREE ? LOGM : 11>::TT : T::TT;
+  constexpr int BUFL = THREE ? Team3<THREE ? LOGM : 11>::BUF : T::BUF;
   const int t = threadIdx.x;
   const int nb = gd.band_end - gd.band_begin;
-  const int bl = t / T::TT;
-  const int tt = t - bl * T::TT;
+  const int bl = t / TT;
+  const int tt = t - bl * TT;
   const bool active = bl < nb;
   const BandDesc bd = a.bands[gd.band_begin + (active ? bl : 0)];
   const int twoN = 2 * a.N;
   float2* s_tw = sm;
   float2* s_x0 = sm + M;
   float2* s_x1 = s_x0 + gd.fp_len;
-  float2* buf = s_x1 + gd.fp_len + bl * T::BUF;
+  float2* buf = s_x1 + gd.fp_len + bl * BUFL;
   const float* __restrict__ g = a.win + bd.win_off;
-  for (int i = t; i < M; i += blockDim.x) s_tw[i] = __ldg(a.twband + (M - 16) + i);
+  if (!THREE)
+    for (int i = t; i < M; i += blockDim.x) s_tw[i] = __ldg(a.twband + (M - 16) + i);
   auto stage = [&](int64_t s, float2* dst) {
     const float2* src = a.spec + s * a.spec_stride + gd.fp_lo;
     for (int i = 2 * t; i < gd.fp_len; i += 2 * (int)blockDim.x) cp_async16(dst + i, src + i);
@@ -190,32 +155,38 @@ __device__ void analysis_persistent(const BandArgs& a, const GroupDesc& gd, int 
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();  // this slice's block (and, first time, the twiddles) are in
-    if (active) {
-      // every load is issued; out-of-support residues get weight 0 (the
-      // window table has padding after its last channel)
-      auto load = [&](int idx) -> float2 {
-        const int o = (idx - bd.j0) & (M - 1);
-        const bool in = o < bd.len;
-        const int oc = in ? o : 0;
-        int b = bd.j0 + oc;
-        if (b >= twoN) b -= twoN;
-        const bool mir = b > a.N;
-        float2 x = X[mir ? twoN - b : b];
-        const float w = __ldg(g + oc);
-        if (mir) x.y = -x.y;
-        return c_scale(x, in ? w : 0.f);
-      };
-      team_pass1<LOGM, +1>(tt, buf, load);
+    // every load is issued; out-of-support residues get weight 0 (the
+    // window table has padding after its last channel)
+    auto load = [&](int idx) -> float2 {
+      const int o = (idx - bd.j0) & (M - 1);
+      const bool in = o < bd.len;
+      const int oc = in ? o : 0;
+      int b = bd.j0 + oc;
+      if (b >= twoN) b -= twoN;
+      const bool mir = b > a.N;
+      float2 x = X[mir ? twoN - b : b];
+      const float w = __ldg(g + oc);
+      if (mir) x.y = -x.y;
+      return c_scale(x, in ? w : 0.f);
+    };
+    if constexpr (THREE) {
+      float2* out = a.coef + s * a.cps + bd.coef_off;
+      band_three_pass<LOGM, +1>(active, tt, buf, a.tw4096, load,
+                                [&](int i, float2 v) { __stcs(out + i, v); });
+      __syncthreads();
+      continue;
     }
+    if (active) team_pass1<THREE ? 4 : LOGM, +1>(tt, buf, load);
     __syncwarp();  // a team lies inside one warp
     if (active) {
       float2 res[T::HELD];
-      team_pass2<LOGM, +1>(tt, buf, [&](int j, int r) { return c_conj(s_tw[r * T::R1 + j]); }, res);
+      constexpr int LP = THREE ? 10 : LOGM;
+      team_pass2<LP, +1>(tt, buf, [&](int j, int r) { return c_conj(s_tw[r * T::R1 + j]); }, res);
       float2* out = a.coef + s * a.cps + bd.coef_off;
 #pragma unroll
       for (int i = 0; i < T::J2; ++i)
 #pragma unroll
-        for (int r = 0; r < T::R2; ++r) __stcs(out + team_out_index<LOGM>(tt, i, r), res[i * T::R2 + r]);
+        for (int r = 0; r < T::R2; ++r) __stcs(out + team_out_index<LP>(tt, i, r), res[i * T::R2 + r]);
     }
     __syncthreads();  // the footprint buffer is refilled two slices later
   }
@@ -237,6 +208,8 @@ __global__ void __launch_bounds__(kBandThreads, 1) band_analysis_persistent_kern
     case 8: analysis_persistent<8>(a, gd, gl.y, lanes, total, sm); break;
     case 9: analysis_persistent<9>(a, gd, gl.y, lanes, total, sm); break;
     case 10: analysis_persistent<10>(a, gd, gl.y, lanes, total, sm); break;
+    case 11: analysis_persistent<11>(a, gd, gl.y, lanes, total, sm); break;
+    case 12: analysis_persistent<12>(a, gd, gl.y, lanes, total, sm); break;
   }
 }
 
@@ -326,6 +299,19 @@ __global__ void __launch_bounds__(kBandThreads) band_synthesis_kernel(BandArgs a
     s_gb[t] = GatherBand{b.dlo, b.dhi, b.j0, b.smem_off};
   }
   __syncthreads();  // tables filled by all threads; the passes only sync per warp
+  if (gd.log2M > kMaxTwoPassLog2) {
+    // three-pass lengths: the team spans warps; its last pass writes Y w g~ at
+    // the support offsets into the band's buffer
+    const float2* c = a.coef + s * a.cps + bd.coef_off;
+    auto in = [&](int idx) { return __ldcs(c + idx); };
+    const float* __restrict__ g = a.win + bd.win_off;
+    auto contrib = [&](int idx, float2 v) {  // weighted as in the two-pass path
+      const int o = (idx - bd.j0) & ((1 << bd.log2M) - 1);
+      if (o < bd.len) buf[o] = c_scale(v, __ldg(g + o));
+    };
+    if (gd.log2M == 11) band_three_pass<11, -1>(k >= 0, tt, buf, a.tw4096, in, contrib);
+    else band_three_pass<12, -1>(k >= 0, tt, buf, a.tw4096, in, contrib);
+  }
   if (k >= 0) {
     const float2* c = a.coef + s * a.cps + bd.coef_off;
     switch (bd.log2M) {
@@ -431,6 +417,7 @@ BandArgs make_args(const slicq_plan* pl, const Workspace& ws, const float* win) 
   a.mirror_list = pl->d_mirror_list;
   a.win = win;
   a.twband = pl->d_twband;
+  a.tw4096 = pl->d_tw4096;
   a.spec = ws.spec;
   a.spec_stride = ws.spec_stride;
   a.cps = pl->coefs_per_slice;

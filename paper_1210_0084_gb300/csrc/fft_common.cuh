@@ -193,6 +193,45 @@ struct SmemTwiddles {
   }
 };
 
+// ------------------------------------------- three-pass Stockham (team) ---
+// Lengths 2^11 and 2^12 (radices 16, 16, 8 or 16): a team of L/32 threads,
+// 32 values each, spanning several warps.  Pass p reads in(j + r L/R) for
+// its j values, twiddles by W_{Ns R}^{(j mod Ns) r} (Ns = product of the
+// earlier radices), transforms and writes out((j/Ns) Ns R + (j mod Ns) + r Ns).
+// `sync()` runs between the reads and the writes of a pass so that a pass can
+// read and write the same buffer.
+template <int LOGL>
+struct Team3 {
+  static constexpr int L = 1 << LOGL;
+  static constexpr int R0 = 16, R1 = 16, R2 = L / 256;
+  static constexpr int TT = L / 32;
+  static constexpr int BUF = L + 1;  // odd length (bank spread between channels)
+};
+
+template <int L, int R, int NS, int SIGN, int TT, class In, class Tw, class Sync, class Out>
+__device__ __forceinline__ void stockham_pass(int tt, In in, Tw tw, Sync sync, Out out) {
+  constexpr int J = (L / R) / TT;
+  float2 v[J][R];
+#pragma unroll
+  for (int i = 0; i < J; ++i)
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[i][r] = in(tt + TT * i + r * (L / R));
+  sync();
+#pragma unroll
+  for (int i = 0; i < J; ++i) {
+    const int j = tt + TT * i;
+    const int jm = j % NS;
+    if (NS > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) v[i][r] = c_mul(v[i][r], tw(jm * r, NS * R));
+    }
+    dft_reg<R, SIGN>(v[i]);
+    const int o = (j / NS) * NS * R + jm;
+#pragma unroll
+    for (int r = 0; r < R; ++r) out(o + r * NS, v[i][r]);
+  }
+}
+
 // Element index of res[i * R2 + r] after team_pass2.
 template <int LOGL>
 __device__ __forceinline__ int team_out_index(int tt, int i, int r) {

@@ -14,7 +14,8 @@ namespace slicq {
 // Threads of one band-group CTA, and complex values each thread holds.
 constexpr int kBandThreads = 256;
 constexpr int kPerThread = 32;
-constexpr int kMaxBandLog2 = 10;  // M_k <= 1024 (two register passes of <= 32)
+constexpr int kMaxTwoPassLog2 = 10;  // M_k <= 1024: two register passes of <= 32
+constexpr int kMaxBandLog2 = 12;     // M_k <= 4096: three passes (16, 16, <= 16)
 constexpr int kMinBandLog2 = 4;   // M_k >= 16
 constexpr int kSliceMaxThreads = 256;  // slice kernels: N / (32 C) <= 256
 constexpr int64_t kMaxGridY = 65535;
@@ -115,6 +116,7 @@ struct slicq_plan {
   float2* d_tw_hi = nullptr;  // exp(-2 pi i (t << tw_lb) / 2N)
   float2* d_twband = nullptr; // band pass-2 twiddles, per length, [r][j] layout
   float2* d_tw4 = nullptr;    // four-step twiddles exp(-2 pi i q u / N) at [u Q + q]
+  float2* d_tw4096 = nullptr; // exp(-2 pi i t / 4096), t < 4096
 
   // optional kernel timing trace (events around every launch)
   struct Trace {

@@ -156,7 +156,8 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
         const int lm = pl->bands[k].log2M;
         const int M = 1 << lm;
         const int need_t = M >= kPerThread ? M / kPerThread : 1;
-        const int need_s = M + (M >> ((lm + 1) / 2)) + 1;  // Team<lm>::BUF
+        const int need_s = lm > kMaxTwoPassLog2 ? M + 1                 // Team3<lm>::BUF
+                                                : M + (M >> ((lm + 1) / 2)) + 1;  // Team<lm>::BUF
         if (threads + need_t > kBandThreads) break;
         // one band length per group: every warp of the CTA runs the same code
         if (k > gd.band_begin && lm != pl->bands[gd.band_begin].log2M) break;
@@ -198,7 +199,8 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
       {
         const int M = 1 << gd.log2M;
         const int nb = gd.band_end - gd.band_begin;
-        const int bufl = M + (M >> ((gd.log2M + 1) / 2)) + 1;  // Team<log2M>::BUF
+        const int bufl = gd.log2M > kMaxTwoPassLog2 ? M + 1
+                                                    : M + (M >> ((gd.log2M + 1) / 2)) + 1;
         in_a = std::max(in_a, gd.fp_len);
         in_s = std::max(in_s, nb * M);
         tb_max = std::max(tb_max, nb * bufl);
@@ -371,7 +373,7 @@ __global__ void k_duals(const WinJob* jobs, int nch, int64_t total, const double
 // pass-2 tables of the band lengths 16..1024 ([r][j] per length); and the
 // four-step twiddles exp(-2 pi i q u / N) at [u Q + q]
 __global__ void k_twiddles(int64_t L2, int lb, int logQ, float2* lo, float2* hi, float2* tband,
-                           float2* t4) {
+                           float2* t4, float2* t4096) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   const int64_t nlo = int64_t(1) << lb;
   const int64_t nhi = L2 >> lb;
@@ -394,6 +396,10 @@ __global__ void k_twiddles(int64_t L2, int lb, int logQ, float2* lo, float2* hi,
     const int64_t r = e / R1, j = e % R1;
     sincospi(-2.0 * (double)((j * r) % M) / (double)M, &s, &c);
     tband[i] = make_float2((float)c, (float)s);
+  }
+  if (i < 4096) {
+    sincospi(-2.0 * (double)i / 4096.0, &s, &c);
+    t4096[i] = make_float2((float)c, (float)s);
   }
   if (i < N) {
     const int64_t u = i >> logQ, q = i & ((int64_t(1) << logQ) - 1);
@@ -469,6 +475,7 @@ slicq_status build_tables(slicq_plan* pl) {
   const size_t o_twhi = take(sizeof(float2) * (L2 >> pl->tw_lb));
   const size_t o_twband = take(sizeof(float2) * 2032);
   const size_t o_tw4 = take(sizeof(float2) * pl->N);
+  const size_t o_tw4096 = take(sizeof(float2) * 4096);
   if (cudaMalloc(&pl->d_arena, off) != cudaSuccess) return SLICQ_ENOMEM;
   char* base = (char*)pl->d_arena;
   pl->d_bands = (BandDesc*)(base + o_bands);
@@ -487,6 +494,7 @@ slicq_status build_tables(slicq_plan* pl) {
   pl->d_tw_hi = (float2*)(base + o_twhi);
   pl->d_twband = (float2*)(base + o_twband);
   pl->d_tw4 = (float2*)(base + o_tw4);
+  pl->d_tw4096 = (float2*)(base + o_tw4096);
 
   slicq_status st = SLICQ_OK;
   cudaError_t e = cudaSuccess;
@@ -553,9 +561,9 @@ slicq_status build_tables(slicq_plan* pl) {
     }
     if (e == cudaSuccess) {
       const int64_t nt = std::max<int64_t>(std::max<int64_t>(int64_t(1) << pl->tw_lb, L2 >> pl->tw_lb),
-                                           std::max<int64_t>(2032, pl->N));
+                                           std::max<int64_t>(4096, pl->N));
       k_twiddles<<<(unsigned)((nt + T - 1) / T), T>>>(L2, pl->tw_lb, pl->logQ, pl->d_tw_lo, pl->d_tw_hi,
-                                                      pl->d_twband, pl->d_tw4);
+                                                      pl->d_twband, pl->d_tw4, pl->d_tw4096);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) {

@@ -61,6 +61,8 @@ SMALL = [
     (16000.0, 50.0, 8000.0, 24, 2048, 512, 1500, 1),       # n < 2N: two slices
     (44100.0, 40.0, 22050.0, 48, 8192, 2048, 30000, 2),    # several channels cross DC
     (48000.0, 50.0, 22000.0, 96, 4096, 1024, 20000, 1),    # ~90 widened channels cross DC
+    (48000.0, 50.0, 22000.0, 24, 16384, 4096, 60000, 1),   # Nyquist plateau of M = 2048
+    (48000.0, 50.0, 20000.0, 24, 16384, 4096, 50000, 2),   # Nyquist plateau of M = 4096
 ]
 
 
