@@ -389,17 +389,18 @@ __global__ void __launch_bounds__(kBandThreads) band_synthesis_kernel(BandArgs a
     if (bd_i < 0) continue;
     const BoundaryDesc b = a.bounds[bd_i];
     const int64_t slot = s * (a.G - 1) + bd_i;
-    // every thread makes its own slot writes visible before the counter moves
-    __threadfence();
+    // barrier, then one thread fences and moves the counter (the pattern of
+    // a grid-wide barrier): the CTA's slot writes are ordered before it
     __syncthreads();
     if (t == 0) {
+      __threadfence();
       // 0 -> 1 for the first arriver, 1 -> 0 for the second (ready for the next call)
       const unsigned old = atomicInc(a.cnt + slot, 1u);
+      __threadfence();
       s_flag = (old == 1u);
     }
     __syncthreads();
     if (s_flag) {
-      __threadfence();
       const float2* p0 = a.patch + (slot * 2 + 0) * a.max_ovl;
       const float2* p1 = a.patch + (slot * 2 + 1) * a.max_ovl;
       for (int h = b.lo + t; h < b.hi; h += blockDim.x)

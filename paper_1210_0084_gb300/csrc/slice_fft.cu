@@ -228,25 +228,30 @@ __global__ void __launch_bounds__(kSliceMaxThreads) slice_forward_kernel(SliceAr
   if (blockIdx.x == 0 && threadIdx.x == 0) *a.items = 0ull;
   const SmemTwiddles tws = stage_twiddles(a, sm);
   __syncthreads();
+  const int Pc = 1 << a.logPc;
   {
     float2 res[TQ::HELD];
     int ul, tt;
     fourstep<LOGP, LOGQ, -1>(a, cluster, sm, tws, load, res, ul, tt);
     __syncthreads();
-    // Z rows to shared memory for the even/odd split (needs Z[N - k])
+    // Z to shared memory, column-major [v][ul], for the even/odd split (needs
+    // Z[N - k] from the partner row): local reads, partner reads and the
+    // stores of X are then all contiguous across a warp
 #pragma unroll
     for (int i = 0; i < TQ::J2; ++i)
 #pragma unroll
       for (int r = 0; r < TQ::R2; ++r)
-        sm[ul * G::ZS3 + team_out_index<LOGQ>(tt, i, r)] = res[i * TQ::R2 + r];
+        sm[team_out_index<LOGQ>(tt, i, r) * Pc + ul] = res[i * TQ::R2 + r];  // [v][ul]
   }
   cluster.sync();
 
   // X[k], k = u + P v for this CTA's rows u; X[N] from k = 0
-  const int Pc = 1 << a.logPc;
   const int rank = (int)cluster.block_rank();
   float2* X = a.spec + s * a.spec_stride;
   const int held = Pc * G::Q;
+  // unrolled so that several partner loads from distributed shared memory
+  // are in flight at once
+#pragma unroll 8
   for (int idx = threadIdx.x; idx < held; idx += blockDim.x) {
     const int ul = idx & (Pc - 1);
     const int v = idx >> a.logPc;
@@ -256,8 +261,8 @@ __global__ void __launch_bounds__(kSliceMaxThreads) slice_forward_kernel(SliceAr
     if (u == 0) { up = 0; vp = (G::Q - v) & (G::Q - 1); }
     else { up = G::P - u; vp = G::Q - 1 - v; }
     const float2* rsm = cluster.map_shared_rank(sm, up >> a.logPc);
-    const float2 zp = c_conj(rsm[(up & (Pc - 1)) * G::ZS3 + vp]);
-    const float2 z = sm[ul * G::ZS3 + v];
+    const float2 zp = c_conj(rsm[vp * Pc + (up & (Pc - 1))]);
+    const float2 z = sm[v * Pc + ul];
     // even part E = (Z[k] + conj Z[N-k]) / 2, odd part O = (Z[k] - conj Z[N-k]) / 2i
     const float2 E = c_scale(c_add(z, zp), 0.5f);
     const float2 D = c_sub(z, zp);
@@ -265,7 +270,10 @@ __global__ void __launch_bounds__(kSliceMaxThreads) slice_forward_kernel(SliceAr
     X[k] = c_add(E, c_mul(tws((uint32_t)k), O));
     if (k == 0) X[a.N] = c_sub(E, O);
   }
-  cluster.sync();  // keep this CTA's shared memory alive for its neighbours
+  // keep this CTA's shared memory alive until its neighbours' partner loads
+  // are done (their values are consumed, so no memory ordering is needed)
+  asm volatile("barrier.cluster.arrive.relaxed.aligned;\n" ::: "memory");
+  asm volatile("barrier.cluster.wait.aligned;\n" ::: "memory");
 }
 
 // ------------------------------------------------------------- inverse ---
@@ -279,15 +287,17 @@ __device__ __forceinline__ void ola_combine(const SliceArgs& a, int64_t tr_slot,
   float* mine = a.ola_patch + (tr_slot * 2 + side) * (int64_t)a.Mtr;
   const float* other = a.ola_patch + (tr_slot * 2 + (1 - side)) * (int64_t)a.Mtr;
   each([&](int o, int tpos, float v) { mine[o] = v; });
-  __threadfence();
+  // barrier, then one thread fences and moves the counter (the pattern of a
+  // grid-wide barrier): the CTA's slot writes are ordered before it
   __syncthreads();
   if (threadIdx.x == 0) {
+    __threadfence();
     const unsigned old = atomicInc(a.ola_cnt + tr_slot * a.C + rank, 1u);
+    __threadfence();
     *s_flag = (old == 1u);
   }
   __syncthreads();
   if (*s_flag) {
-    __threadfence();
     each([&](int o, int tpos, float v) {
       if (tpos < n32) out[tpos] = v + __ldcg(other + o);
     });
