@@ -71,13 +71,11 @@ size_t workspace_layout(const slicq_plan* pl, int64_t n, int64_t batch, void* ba
   w.S = w.L / pl->N;
   w.spec_stride = pl->N + 2;
   const int64_t slices = batch * w.S;
-  const int64_t nbd = std::max(pl->G - 1, 0);
   size_t off = 0;
   auto take = [&](size_t bytes) { const size_t o = off; off = align256(off + bytes); return o; };
   const size_t o_items = take(2 * sizeof(unsigned long long));
   const size_t o_spec = take(sizeof(float2) * slices * w.spec_stride);
-  const size_t o_bp = take(sizeof(float2) * slices * nbd * 2 * pl->max_ovl);
-  const size_t o_bc = take(sizeof(uint32_t) * slices * nbd);
+  const size_t o_bp = take(sizeof(float2) * slices * 2 * std::max(pl->ovl_total, 1));
   const size_t o_op = take(sizeof(float) * slices * 2 * pl->params.trans_len);
   const size_t o_oc = take(sizeof(uint32_t) * slices * pl->C);
   w.bytes = off;
@@ -86,7 +84,6 @@ size_t workspace_layout(const slicq_plan* pl, int64_t n, int64_t batch, void* ba
     w.items = (unsigned long long*)(b + o_items);
     w.spec = (float2*)(b + o_spec);
     w.band_patch = (float2*)(b + o_bp);
-    w.band_cnt = (uint32_t*)(b + o_bc);
     w.ola_patch = (float*)(b + o_op);
     w.ola_cnt = (uint32_t*)(b + o_oc);
   }
@@ -99,13 +96,11 @@ size_t workspace_layout_rows(const slicq_plan* pl, int64_t rows, void* base, Wor
   w.S = rows;
   w.L = 0;
   w.spec_stride = pl->N + 2;
-  const int64_t nbd = std::max(pl->G - 1, 0);
   size_t off = 0;
   auto take = [&](size_t bytes) { const size_t o = off; off = align256(off + bytes); return o; };
   const size_t o_items = take(2 * sizeof(unsigned long long));
   const size_t o_spec = take(sizeof(float2) * rows * w.spec_stride);
-  const size_t o_bp = take(sizeof(float2) * rows * nbd * 2 * pl->max_ovl);
-  const size_t o_bc = take(sizeof(uint32_t) * rows * nbd);
+  const size_t o_bp = take(sizeof(float2) * rows * 2 * std::max(pl->ovl_total, 1));
   const size_t o_op = take(sizeof(float) * rows * 2 * pl->params.trans_len);
   const size_t o_oc = take(sizeof(uint32_t) * rows * pl->C);
   w.bytes = off;
@@ -114,7 +109,6 @@ size_t workspace_layout_rows(const slicq_plan* pl, int64_t rows, void* base, Wor
     w.items = (unsigned long long*)(b + o_items);
     w.spec = (float2*)(b + o_spec);
     w.band_patch = (float2*)(b + o_bp);
-    w.band_cnt = (uint32_t*)(b + o_bc);
     w.ola_patch = (float*)(b + o_op);
     w.ola_cnt = (uint32_t*)(b + o_oc);
   }
@@ -251,6 +245,8 @@ static slicq_status synthesis(const slicq_plan* plan, const float* d_coef, int64
   return on_device(plan, [&] {
     cudaError_t e = traced(plan, 2, stream, [&] {
       return launch_band_synthesis(plan, reinterpret_cast<const float2*>(d_coef), batch, kind, ws, stream); });
+    if (e == cudaSuccess && plan->ovl_total > 0)
+      e = traced(plan, 4, stream, [&] { return launch_band_boundaries(plan, batch, ws, stream); });
     if (e == cudaSuccess)
       e = traced(plan, 3, stream, [&] {
         return launch_slice_inverse(plan, n_samples, batch, kind, ws, d_out, stream); });

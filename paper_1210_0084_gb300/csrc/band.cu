@@ -9,12 +9,15 @@
 // slice kernel, bins beyond N are read as conjugates.
 //
 // Synthesis (Algorithm 2, loop over k and line "sum_k f_k g~_k"): Y = forward
-// DFT_{M_k}(c_k); each channel writes its weighted values Y[j mod M_k] w g~_k[j]
-// (j in J_k) to shared memory; then every half-spectrum bin h = 0..N of the
-// group sums, in a fixed order, the channels whose support covers h directly
-// and the conjugates of those covering -h.  Bins shared with the neighbouring
-// group are combined by whichever of the two CTAs arrives second
-// (a + b == b + a), so the result is deterministic and needs no zero-fill.
+// DFT_{M_k}(c_k); each channel's weighted values Y[j mod M_k] w g~_k[j]
+// (j in J_k) belong to half-spectrum bin j for j <= N and, conjugated, to bin
+// 2N - j for j >= N or j = 0 (the mirrored channel's term for a real signal).
+// At plan time the channels of a group are coloured so that channels of one
+// colour touch disjoint bins; each colour is an accumulator layer in shared
+// memory that its channels fill with plain stores, and every bin is the sum
+// of its layers in a fixed order.  Bins shared with the neighbouring group go
+// to two patch rows that a second kernel adds (a + b): the result is
+// deterministic without atomics.
 #include "fft_common.cuh"
 #include "internal.h"
 
@@ -31,7 +34,8 @@ struct BandArgs {
   const GroupDesc* __restrict__ groups;
   const BoundaryDesc* __restrict__ bounds;
   const int16_t* __restrict__ thread_band;
-  const int32_t* __restrict__ mirror_list;  // channels with mirrored bins, per group
+  const int32_t* __restrict__ ovl_start;    // [G] boundary offsets in a patch row
+  const int32_t* __restrict__ ovl_bin;      // [ovl_total] bin of each patch-row entry
   const float* __restrict__ win;     // window table of this launch
   const float2* __restrict__ twband; // pass-2 twiddle tables, kTwSmall entries
   const float2* __restrict__ tw4096; // exp(-2 pi i t / 4096), t < 4096 (three-pass lengths)
@@ -41,9 +45,8 @@ struct BandArgs {
   int64_t spec_stride;
   float2* coef;                      // [slice][cps]
   int64_t cps;
-  float2* patch;                     // [slice][G-1][2][max_ovl]
-  uint32_t* cnt;                     // [slice][G-1]
-  int G, max_ovl;
+  float2* patch;                     // [slice][2][ovl_total]
+  int ovl_total;
   int N;
 };
 
@@ -215,12 +218,6 @@ __global__ void __launch_bounds__(kBandThreads, 1) band_analysis_persistent_kern
 
 // ----------------------------------------------------------- synthesis ---
 
-// Per-channel fields the gather needs, staged in shared memory.
-struct GatherBand {
-  int32_t dlo, dhi;   // direct bins [dlo, dhi] (dhi < 0: none)
-  int32_t j0, base;   // support start on the circle, contribution offset in smem
-};
-
 template <int LOGM>
 __device__ __forceinline__ void synthesis_pass1(int tt, const float2* __restrict__ c, float2* buf) {
   team_pass1<LOGM, -1>(tt, buf, [&](int idx) { return __ldcs(c + idx); });
@@ -232,57 +229,87 @@ __device__ __forceinline__ void synthesis_pass2(int tt, const float2* s_tw, cons
   team_pass2<LOGM, -1>(tt, buf, BandTw<LOGM, -1>{s_tw}, res);
 }
 
-// Weighted values Y[j mod M] w g~[j] stored at their support offsets o = j - j0.
+// Stores the thread's values Y[idx] w g~[o] (o = idx - j0 mod M < |J_k|) to
+// the channel's layers: layer[dl][j] for the direct bins, layer[ml][2N - j]
+// (conjugated) for the mirrored ones.  layer(l) points at layer l, indexed by
+// bin.  The window loads are unconditional (index clamped) so that they are
+// all in flight together.
 template <int LOGM>
-__device__ __forceinline__ void synthesis_weight(const BandArgs& a, const BandDesc& bd, int tt,
-                                                 const float2* res, float2* contrib) {
+__device__ __forceinline__ void store_held(const BandArgs& a, const BandDesc& bd, int tt,
+                                           const float2* res, float2* dl, float2* ml) {
   using T = Team<LOGM>;
   constexpr int M = 1 << LOGM;
   const float* __restrict__ g = a.win + bd.win_off;
+  const int twoN = 2 * a.N;
 #pragma unroll
   for (int i = 0; i < T::J2; ++i)
 #pragma unroll
     for (int r = 0; r < T::R2; ++r) {
-      const int idx = team_out_index<LOGM>(tt, i, r);
-      const int o = (idx - bd.j0) & (M - 1);
-      if (o < bd.len) contrib[o] = c_scale(res[i * T::R2 + r], __ldg(g + o));
+      const int o = (team_out_index<LOGM>(tt, i, r) - bd.j0) & (M - 1);
+      const bool in = o < bd.len;
+      const float2 y = c_scale(res[i * T::R2 + r], __ldg(g + (in ? o : 0)));
+      int b = bd.j0 + o;
+      if (b >= twoN) b -= twoN;
+      if (in && b <= a.N) dl[b] = y;
+      if (in && (b == 0 || b >= a.N)) ml[b == 0 ? 0 : twoN - b] = c_conj(y);
     }
 }
 
-// Sum of all contributions to half-spectrum bin h, in a fixed order: direct
-// channels from the highest covering one down, then the mirrored channels.
-__device__ __forceinline__ float2 gather_bin(int h, int& last, int nb, const GatherBand* gb,
-                                             const GroupDesc& gd, const BandDesc* __restrict__ bands,
-                                             const int32_t* __restrict__ mirror_list,
-                                             const float2* sm, int twoN) {
-  while (last + 1 < nb && gb[last + 1].dlo <= h) ++last;
-  float2 acc = make_float2(0.f, 0.f);
-  for (int k = last; k >= 0; --k) {
-    const GatherBand b = gb[k];
-    if (b.dhi < 0) continue;          // channel without support
-    if (b.dhi < h) break;             // dhi is non-decreasing over the group
-    int o = h - b.j0;
-    if (o < 0) o += twoN;
-    acc = c_add(acc, sm[b.base + o]);
+__device__ __forceinline__ void store_held_m(int log2M, const BandArgs& a, const BandDesc& bd, int tt,
+                                             const float2* res, float2* dl, float2* ml) {
+  switch (log2M) {
+    case 4: store_held<4>(a, bd, tt, res, dl, ml); break;
+    case 5: store_held<5>(a, bd, tt, res, dl, ml); break;
+    case 6: store_held<6>(a, bd, tt, res, dl, ml); break;
+    case 7: store_held<7>(a, bd, tt, res, dl, ml); break;
+    case 8: store_held<8>(a, bd, tt, res, dl, ml); break;
+    case 9: store_held<9>(a, bd, tt, res, dl, ml); break;
+    case 10: store_held<10>(a, bd, tt, res, dl, ml); break;
   }
-  for (int i = 0; i < gd.nmirror; ++i) {
-    const BandDesc bd = bands[mirror_list[gd.mirror_off + i]];
-    if (h < bd.mlo || h > bd.mhi) continue;
-    const int bm = h == 0 ? 0 : twoN - h;
-    int o = bm - bd.j0;
-    if (o < 0) o += twoN;
-    if (o < bd.len) acc = c_add(acc, c_conj(sm[bd.smem_off + o]));
-  }
-  return acc;
 }
 
-__global__ void __launch_bounds__(kBandThreads) band_synthesis_kernel(BandArgs a) {
-  extern __shared__ float2 sm[];
+// Zeroes n complex values at p (p 16-byte aligned) with 16-byte stores.
+__device__ __forceinline__ void zero_layers(float2* p, int n) {
+  float4* q = reinterpret_cast<float4*>(p);
+  const int n4 = n >> 1;
+  const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
+  int i = threadIdx.x;
+  for (; i + 3 * kBandThreads < n4; i += 4 * kBandThreads) {
+    q[i] = z;
+    q[i + kBandThreads] = z;
+    q[i + 2 * kBandThreads] = z;
+    q[i + 3 * kBandThreads] = z;
+  }
+  for (; i < n4; i += kBandThreads) q[i] = z;
+  if ((n & 1) && threadIdx.x == 0) p[n - 1] = make_float2(0.f, 0.f);
+}
+
+// Bins [acc_lo, acc_hi): the sum of the NL layers (fixed order) to the
+// spectrum, or to a patch row for bins shared with a neighbouring group.
+template <int NL>
+__device__ __forceinline__ void write_bins(const GroupDesc& gd, const float2* lay, int nl, int acc_n,
+                                           float2* spec, float2* patch_l, float2* patch_r) {
+  for (int h = gd.acc_lo + (int)threadIdx.x; h < gd.acc_hi; h += kBandThreads) {
+    const float2* p = lay + (h - gd.acc_lo);
+    float2 v = p[0];
+    if (NL > 0) {
+#pragma unroll
+      for (int l = 1; l < NL; ++l) v = c_add(v, p[l * acc_n]);
+    } else {
+      for (int l = 1; l < nl; ++l) v = c_add(v, p[l * acc_n]);
+    }
+    if (h < gd.ex_lo) patch_l[h] = v;
+    else if (h >= gd.ex_hi) patch_r[h] = v;
+    else spec[h] = v;
+  }
+}
+
+__global__ void __launch_bounds__(kBandThreads, 2) band_synthesis_kernel(BandArgs a) {
+  extern __shared__ __align__(16) float2 sm[];
   __shared__ float2 s_tw[kTwSmall];
-  __shared__ GatherBand s_gb[kBandThreads];
-  __shared__ int s_flag;
-  const int g = blockIdx.x;
-  const int64_t s = a.slice_base + blockIdx.y;
+  // slices vary fastest: CTAs resident together mostly run one group's code
+  const int g = blockIdx.y;
+  const int64_t s = a.slice_base + blockIdx.x;
   const int t = threadIdx.x;
   const int k = a.thread_band[g * kBandThreads + t];
   const GroupDesc gd = a.groups[g];
@@ -290,123 +317,119 @@ __global__ void __launch_bounds__(kBandThreads) band_synthesis_kernel(BandArgs a
   BandDesc bd{};
   if (k >= 0) bd = a.bands[k];
   const int tt = t - bd.tofs;
+  const int M = 1 << gd.log2M;
+  const bool three = gd.log2M > kMaxTwoPassLog2;
+  // accumulator layers over bins [acc_lo, acc_hi): direct colours first, then
+  // the mirrored ones.  Two-pass teams hold their values in registers when
+  // the layers are filled, so the layers overlay their buffers.
+  const int acc_n = gd.acc_hi - gd.acc_lo;
+  const int nd = gd.nphases & 0xFFFF;
+  const int nl = nd + (gd.nphases >> 16);
+  float2* lay = three ? sm + ((nb * (M + 1) + 1) & ~1) : sm;  // 16-byte aligned
+  // this channel's layers, indexed by bin (a channel without direct or
+  // mirrored bins never writes the corresponding one)
+  const int dli = bd.phases & 0xFFFF, mli = bd.phases >> 16;
+  float2* dl = lay + (dli == kNoPhase ? 0 : dli) * acc_n - gd.acc_lo;
+  float2* ml = lay + (mli == kNoPhase ? 0 : nd + mli) * acc_n - gd.acc_lo;
   float2* buf = sm + bd.smem_off;
-  const int twoN = 2 * a.N;
+  const float2* c = a.coef + s * a.cps + bd.coef_off;
 
-  load_twiddles(a, s_tw);
-  if (t < nb) {
-    const BandDesc b = a.bands[gd.band_begin + t];
-    s_gb[t] = GatherBand{b.dlo, b.dhi, b.j0, b.smem_off};
-  }
-  __syncthreads();  // tables filled by all threads; the passes only sync per warp
-  if (gd.log2M > kMaxTwoPassLog2) {
-    // three-pass lengths: the team spans warps; its last pass writes Y w g~ at
-    // the support offsets into the band's buffer
-    const float2* c = a.coef + s * a.cps + bd.coef_off;
+  if (three) {
+    zero_layers(lay, nl * acc_n);
+    // the team spans warps; its last pass writes Y w g~ at the support offsets
+    const float* __restrict__ gw = a.win + bd.win_off;
     auto in = [&](int idx) { return __ldcs(c + idx); };
-    const float* __restrict__ g = a.win + bd.win_off;
-    auto contrib = [&](int idx, float2 v) {  // weighted as in the two-pass path
-      const int o = (idx - bd.j0) & ((1 << bd.log2M) - 1);
-      if (o < bd.len) buf[o] = c_scale(v, __ldg(g + o));
+    auto contrib = [&](int idx, float2 v) {
+      const int o = (idx - bd.j0) & (M - 1);
+      if (o < bd.len) buf[o] = c_scale(v, __ldg(gw + o));
     };
     if (gd.log2M == 11) band_three_pass<11, -1>(k >= 0, tt, buf, a.tw4096, in, contrib);
     else band_three_pass<12, -1>(k >= 0, tt, buf, a.tw4096, in, contrib);
-  }
-  if (k >= 0) {
-    const float2* c = a.coef + s * a.cps + bd.coef_off;
-    switch (bd.log2M) {
-      case 4: synthesis_pass1<4>(tt, c, buf); break;
-      case 5: synthesis_pass1<5>(tt, c, buf); break;
-      case 6: synthesis_pass1<6>(tt, c, buf); break;
-      case 7: synthesis_pass1<7>(tt, c, buf); break;
-      case 8: synthesis_pass1<8>(tt, c, buf); break;
-      case 9: synthesis_pass1<9>(tt, c, buf); break;
-      case 10: synthesis_pass1<10>(tt, c, buf); break;
+    __syncthreads();
+    if (k >= 0) {
+      const int twoN = 2 * a.N;
+      for (int o = tt; o < bd.len; o += M / kPerThread) {
+        int b = bd.j0 + o;
+        if (b >= twoN) b -= twoN;
+        const float2 y = buf[o];
+        if (b <= a.N) dl[b] = y;
+        if (b == 0 || b >= a.N) ml[b == 0 ? 0 : twoN - b] = c_conj(y);
+      }
     }
-  }
-  __syncwarp();  // a team lies inside one warp
-  float2 res[kPerThread];
-  if (k >= 0) {
-    switch (bd.log2M) {
-      case 4: synthesis_pass2<4>(tt, s_tw, buf, res); break;
-      case 5: synthesis_pass2<5>(tt, s_tw, buf, res); break;
-      case 6: synthesis_pass2<6>(tt, s_tw, buf, res); break;
-      case 7: synthesis_pass2<7>(tt, s_tw, buf, res); break;
-      case 8: synthesis_pass2<8>(tt, s_tw, buf, res); break;
-      case 9: synthesis_pass2<9>(tt, s_tw, buf, res); break;
-      case 10: synthesis_pass2<10>(tt, s_tw, buf, res); break;
+  } else {
+    // pass-2 twiddles of this group's length only (pass 1 does not need them:
+    // the barrier after it covers the staging)
+    for (int i = t; i < M; i += blockDim.x) s_tw[(M - 16) + i] = __ldg(a.twband + (M - 16) + i);
+    if (k >= 0) {
+      switch (bd.log2M) {
+        case 4: synthesis_pass1<4>(tt, c, buf); break;
+        case 5: synthesis_pass1<5>(tt, c, buf); break;
+        case 6: synthesis_pass1<6>(tt, c, buf); break;
+        case 7: synthesis_pass1<7>(tt, c, buf); break;
+        case 8: synthesis_pass1<8>(tt, c, buf); break;
+        case 9: synthesis_pass1<9>(tt, c, buf); break;
+        case 10: synthesis_pass1<10>(tt, c, buf); break;
+      }
     }
-  }
-  __syncwarp();  // the team has read its pass buffer: reuse it for contributions
-  if (k >= 0) {
-    switch (bd.log2M) {
-      case 4: synthesis_weight<4>(a, bd, tt, res, buf); break;
-      case 5: synthesis_weight<5>(a, bd, tt, res, buf); break;
-      case 6: synthesis_weight<6>(a, bd, tt, res, buf); break;
-      case 7: synthesis_weight<7>(a, bd, tt, res, buf); break;
-      case 8: synthesis_weight<8>(a, bd, tt, res, buf); break;
-      case 9: synthesis_weight<9>(a, bd, tt, res, buf); break;
-      case 10: synthesis_weight<10>(a, bd, tt, res, buf); break;
+    __syncthreads();  // twiddles staged; pass-1 outputs in the team buffers
+    float2 res[kPerThread];
+    if (k >= 0) {
+      switch (bd.log2M) {
+        case 4: synthesis_pass2<4>(tt, s_tw, buf, res); break;
+        case 5: synthesis_pass2<5>(tt, s_tw, buf, res); break;
+        case 6: synthesis_pass2<6>(tt, s_tw, buf, res); break;
+        case 7: synthesis_pass2<7>(tt, s_tw, buf, res); break;
+        case 8: synthesis_pass2<8>(tt, s_tw, buf, res); break;
+        case 9: synthesis_pass2<9>(tt, s_tw, buf, res); break;
+        case 10: synthesis_pass2<10>(tt, s_tw, buf, res); break;
+      }
     }
+    __syncthreads();  // every team has read its buffer
+    zero_layers(lay, nl * acc_n);
+    __syncthreads();
+    if (k >= 0) store_held_m(gd.log2M, a, bd, tt, res, dl, ml);
   }
   __syncthreads();
 
-  // gather bins [acc_lo, acc_hi); bins shared with a neighbour go to hand-off slots
+  // bins of this group alone to the spectrum, shared bins to the patch rows
+  // (side 0: the lower group of a boundary, side 1: the upper one)
   float2* spec = a.spec + s * a.spec_stride;
-  int bl_hi = gd.acc_lo, br_lo = gd.acc_hi;
+  float2* row = a.patch + s * 2 * (int64_t)a.ovl_total;
   float2* patch_l = nullptr;
   float2* patch_r = nullptr;
-  if (gd.left_bd >= 0) {
-    bl_hi = a.bounds[gd.left_bd].hi;
-    patch_l = a.patch + ((s * (a.G - 1) + gd.left_bd) * 2 + 1) * a.max_ovl - gd.acc_lo;
+  if (gd.left_bd >= 0) patch_l = row + a.ovl_total + a.ovl_start[gd.left_bd] - gd.acc_lo;
+  if (gd.right_bd >= 0) patch_r = row + a.ovl_start[gd.right_bd] - gd.ex_hi;
+  switch (nl) {
+    case 1: write_bins<1>(gd, lay, nl, acc_n, spec, patch_l, patch_r); break;
+    case 2: write_bins<2>(gd, lay, nl, acc_n, spec, patch_l, patch_r); break;
+    case 3: write_bins<3>(gd, lay, nl, acc_n, spec, patch_l, patch_r); break;
+    case 4: write_bins<4>(gd, lay, nl, acc_n, spec, patch_l, patch_r); break;
+    default: write_bins<0>(gd, lay, nl, acc_n, spec, patch_l, patch_r); break;
   }
-  if (gd.right_bd >= 0) {
-    br_lo = a.bounds[gd.right_bd].lo;
-    patch_r = a.patch + ((s * (a.G - 1) + gd.right_bd) * 2 + 0) * a.max_ovl - br_lo;
-  }
-  {
-    int h = gd.acc_lo + t;
-    int last = -1;
-    if (h < gd.acc_hi) {  // last channel with dlo <= h (dlo is non-decreasing)
-      int lo = 0, hi = nb - 1;
-      while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (s_gb[mid].dlo <= h) lo = mid; else hi = mid - 1;
-      }
-      last = s_gb[lo].dlo <= h ? lo : -1;
-    }
-    for (; h < gd.acc_hi; h += blockDim.x) {
-      const float2 v = gather_bin(h, last, nb, s_gb, gd, a.bands, a.mirror_list, sm, twoN);
-      if (h < bl_hi) patch_l[h] = v;
-      else if (h >= br_lo) patch_r[h] = v;
-      else spec[h] = v;
-    }
-  }
-  // hand-offs: the second CTA to arrive at a shared range stores the sums
-#pragma unroll 1
-  for (int side = 0; side < 2; ++side) {
-    const int bd_i = side == 0 ? gd.left_bd : gd.right_bd;
-    if (bd_i < 0) continue;
-    const BoundaryDesc b = a.bounds[bd_i];
-    const int64_t slot = s * (a.G - 1) + bd_i;
-    // barrier, then one thread fences and moves the counter (the pattern of
-    // a grid-wide barrier): the CTA's slot writes are ordered before it
-    __syncthreads();
-    if (t == 0) {
-      __threadfence();
-      // 0 -> 1 for the first arriver, 1 -> 0 for the second (ready for the next call)
-      const unsigned old = atomicInc(a.cnt + slot, 1u);
-      __threadfence();
-      s_flag = (old == 1u);
-    }
-    __syncthreads();
-    if (s_flag) {
-      const float2* p0 = a.patch + (slot * 2 + 0) * a.max_ovl;
-      const float2* p1 = a.patch + (slot * 2 + 1) * a.max_ovl;
-      for (int h = b.lo + t; h < b.hi; h += blockDim.x)
-        spec[h] = c_add(__ldcg(p0 + (h - b.lo)), __ldcg(p1 + (h - b.lo)));
+}
+
+// Bins shared by groups g and g + 1: spectrum = side 0 + side 1.  Thread i
+// takes the i-th bin of the concatenated boundaries (bin number from the
+// plan's table) in kBoundarySlices consecutive slices.
+constexpr int kBoundarySlices = 4;
+
+__global__ void __launch_bounds__(256) band_boundary_kernel(BandArgs a, int64_t total) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= a.ovl_total) return;
+  const int h = __ldg(a.ovl_bin + i);
+  const int64_t s0 = (a.slice_base + blockIdx.y) * kBoundarySlices;
+  float2 p0[kBoundarySlices], p1[kBoundarySlices];
+#pragma unroll
+  for (int u = 0; u < kBoundarySlices; ++u) {
+    if (s0 + u < total) {
+      const float2* row = a.patch + (s0 + u) * 2 * (int64_t)a.ovl_total;
+      p0[u] = __ldcs(row + i);
+      p1[u] = __ldcs(row + a.ovl_total + i);
     }
   }
+#pragma unroll
+  for (int u = 0; u < kBoundarySlices; ++u)
+    if (s0 + u < total) a.spec[(s0 + u) * a.spec_stride + h] = c_add(p0[u], p1[u]);
 }
 
 BandArgs make_args(const slicq_plan* pl, const Workspace& ws, const float* win) {
@@ -415,7 +438,8 @@ BandArgs make_args(const slicq_plan* pl, const Workspace& ws, const float* win) 
   a.groups = pl->d_groups;
   a.bounds = pl->d_bounds;
   a.thread_band = pl->d_thread_band;
-  a.mirror_list = pl->d_mirror_list;
+  a.ovl_start = pl->d_ovl_start;
+  a.ovl_bin = pl->d_ovl_bin;
   a.win = win;
   a.twband = pl->d_twband;
   a.tw4096 = pl->d_tw4096;
@@ -423,9 +447,7 @@ BandArgs make_args(const slicq_plan* pl, const Workspace& ws, const float* win) 
   a.spec_stride = ws.spec_stride;
   a.cps = pl->coefs_per_slice;
   a.patch = ws.band_patch;
-  a.cnt = ws.band_cnt;
-  a.G = pl->G;
-  a.max_ovl = pl->max_ovl;
+  a.ovl_total = pl->ovl_total;
   a.N = (int)pl->N;
   return a;
 }
@@ -450,14 +472,30 @@ cudaError_t launch_band_synthesis(const slicq_plan* pl, const float2* coef, int6
   BandArgs a = make_args(pl, ws, kind == kSynthInverse ? pl->d_gs : pl->d_gadj);
   a.coef = const_cast<float2*>(coef);
   cudaError_t e = cudaFuncSetAttribute(band_synthesis_kernel,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, pl->band_smem_a);
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, pl->band_smem_s);
   if (e != cudaSuccess) return e;
   const int64_t total = batch * ws.S;
   for (int64_t s0 = 0; s0 < total; s0 += kMaxGridY) {
     a.slice_base = s0;
-    dim3 grid(pl->G, (unsigned)(total - s0 < kMaxGridY ? total - s0 : kMaxGridY));
-    band_synthesis_kernel<<<grid, kBandThreads, pl->band_smem_a, st>>>(a);
+    dim3 grid((unsigned)(total - s0 < kMaxGridY ? total - s0 : kMaxGridY), pl->G);
+    band_synthesis_kernel<<<grid, kBandThreads, pl->band_smem_s, st>>>(a);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_band_boundaries(const slicq_plan* pl, int64_t batch, const Workspace& ws,
+                                   cudaStream_t st) {
+  if (pl->ovl_total == 0) return cudaSuccess;
+  BandArgs a = make_args(pl, ws, nullptr);
+  const int64_t total = batch * ws.S;
+  const int64_t chunks = (total + kBoundarySlices - 1) / kBoundarySlices;
+  for (int64_t c0 = 0; c0 < chunks; c0 += kMaxGridY) {
+    a.slice_base = c0;
+    dim3 grid((unsigned)((pl->ovl_total + 255) / 256), (unsigned)(chunks - c0 < kMaxGridY ? chunks - c0 : kMaxGridY));
+    band_boundary_kernel<<<grid, 256, 0, st>>>(a, total);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }

@@ -205,6 +205,7 @@ slicq_status slicq_batch_inverse(const slicq_batch* b, const float* d_coef, floa
     workspace_layout_rows(sb.pl, sb.rows, (char*)d_work + sb.work_off, &ws);
     const float2* coef = reinterpret_cast<const float2*>(d_coef) + sb.coef_off;
     cudaError_t e = launch_band_synthesis(sb.pl, coef, 1, kSynthInverse, ws, sb.st);
+    if (e == cudaSuccess) e = launch_band_boundaries(sb.pl, 1, ws, sb.st);
     if (e == cudaSuccess) e = launch_slice_inverse(sb.pl, 0, 1, kSynthInverse, ws, d_sig_out, sb.st, sb.d_rows);
     return e;
   });

@@ -19,6 +19,9 @@ constexpr int kMaxBandLog2 = 12;     // M_k <= 4096: three passes (16, 16, <= 16
 constexpr int kMinBandLog2 = 4;   // M_k >= 16
 constexpr int kSliceMaxThreads = 256;  // slice kernels: N / (32 C) <= 256
 constexpr int64_t kMaxGridY = 65535;
+// shared memory (complex values) a band group's synthesis may use for its
+// team buffers and accumulator layers; a group closes before exceeding it
+constexpr int kSynSmemBudget = 12288;
 
 // One kept channel k = 0..K+1 on the slice circle Z_{2N} (Sec. 3).
 struct BandDesc {
@@ -31,8 +34,12 @@ struct BandDesc {
   int32_t smem_off;  // complex offset of the team's buffer in shared memory
   int32_t dlo, dhi;  // half-spectrum bins the support covers directly (dhi < 0: none)
   int32_t mlo, mhi;  // half-spectrum bins -j for j in the support (mlo > mhi: none)
-  int32_t pad_;
+  // synthesis accumulator layers: bits 0-15 the layer (colour) of the direct
+  // bins, bits 16-31 the mirrored-bin layer among the group's mirrored ones
+  // (kNoPhase: none).  Channels of one layer touch disjoint bins.
+  int32_t phases;
 };
+constexpr int kNoPhase = 0xFFFF;
 
 // A CTA's worth of consecutive channels for the band kernels.
 struct GroupDesc {
@@ -40,11 +47,9 @@ struct GroupDesc {
   int32_t acc_lo, acc_hi;        // half-spectrum bins the group touches
   int32_t ex_lo, ex_hi;          // bins only this group touches
   int32_t left_bd, right_bd;     // boundary indices, -1 if none
-  int32_t nmirror;               // channels of the group with mirrored bins
-  int32_t mirror_off;            // their indices: mirror_list[mirror_off ..]
   int32_t log2M;                 // every channel of the group has M = 2^log2M
   int32_t fp_lo, fp_len;         // spectrum block the analysis stages (even bounds)
-  int32_t pad_;
+  int32_t nphases;               // direct layers (bits 0-15), mirrored layers (16-31)
 };
 
 // Bins [lo, hi) touched by two neighbouring groups (bd and bd + 1).
@@ -77,6 +82,7 @@ struct slicq_plan {
   int C = 1;              // cluster size of the slice kernels
   int G = 0;              // band groups
   int max_ovl = 0;        // longest group-boundary overlap (bins)
+  int ovl_total = 0;      // bins of all group boundaries of one slice
   int band_smem_a = 0;    // dynamic shared memory of band analysis (bytes)
   int band_smem_s = 0;    // dynamic shared memory of band synthesis (bytes)
   int band_in_a = 0;      // complex values per staged analysis input (max footprint)
@@ -93,8 +99,9 @@ struct slicq_plan {
   std::vector<slicq::BandDesc> bands;
   std::vector<slicq::GroupDesc> groups;
   std::vector<slicq::BoundaryDesc> bounds;
+  std::vector<int32_t> ovl_start;    // [G] prefix sums of the boundary widths
+  std::vector<int32_t> ovl_bin;      // [ovl_total] bin of each entry of a patch row
   std::vector<int16_t> thread_band;  // [G][kBandThreads] channel or -1
-  std::vector<int32_t> mirror_list;  // channels with mirrored bins, grouped by group
   std::vector<double> xi, omega;     // Table 1, channels 0..K+1
   std::vector<int64_t> jlo;          // unwrapped first support sample
 
@@ -103,8 +110,9 @@ struct slicq_plan {
   slicq::BandDesc* d_bands = nullptr;
   slicq::GroupDesc* d_groups = nullptr;
   slicq::BoundaryDesc* d_bounds = nullptr;
+  int32_t* d_ovl_start = nullptr;  // [G]: prefix sums of the boundary widths
+  int32_t* d_ovl_bin = nullptr;    // [ovl_total]: bin of each entry of a patch row
   int16_t* d_thread_band = nullptr;
-  int32_t* d_mirror_list = nullptr;
   float* d_ga = nullptr;    // g_k / sqrt(2N)
   float* d_gs = nullptr;    // w_k g~_k / sqrt(2N)
   float* d_gadj = nullptr;  // g_k / (2 sqrt(2N))
@@ -143,7 +151,6 @@ struct Workspace {
   int64_t spec_stride = 0;         // complex values per slice spectrum row
   float2* spec = nullptr;          // [batch * S][spec_stride]
   float2* band_patch = nullptr;    // [batch * S][G - 1][2][max_ovl]
-  uint32_t* band_cnt = nullptr;    // [batch * S][G - 1]
   float* ola_patch = nullptr;      // [batch * S][2][M]
   uint32_t* ola_cnt = nullptr;     // [batch * S][C]
   size_t bytes = 0;
@@ -160,6 +167,10 @@ cudaError_t launch_band_analysis(const slicq_plan* pl, const Workspace& ws,
 cudaError_t launch_band_synthesis(const slicq_plan* pl, const float2* coef,
                                   int64_t batch, SynthKind kind,
                                   const Workspace& ws, cudaStream_t st);
+// Adds the two partial sums of the bins shared by neighbouring band groups
+// (after launch_band_synthesis, before launch_slice_inverse).
+cudaError_t launch_band_boundaries(const slicq_plan* pl, int64_t batch, const Workspace& ws,
+                                   cudaStream_t st);
 cudaError_t launch_slice_inverse(const slicq_plan* pl, int64_t n,
                                  int64_t batch, SynthKind kind,
                                  const Workspace& ws, float* out,

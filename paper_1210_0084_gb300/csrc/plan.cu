@@ -143,8 +143,7 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
   // ---- band groups: consecutive channels, <= kBandThreads threads each
   pl->groups.clear();
   pl->thread_band.clear();
-  pl->mirror_list.clear();
-  int in_a = 0, in_s = 0, tb_max = 0, smem_p = 0;  // complex values
+  int in_a = 0, in_s = 0, tb_max = 0, smem_p = 0, syn_max = 0;  // complex values
   pl->group_cost.clear();
   {
     int k = 0;
@@ -152,6 +151,17 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
       GroupDesc gd{};
       gd.band_begin = k;
       int threads = 0, smem = 0;
+      // synthesis layers: greedy interval colouring of the direct ranges and
+      // of the mirrored ranges; channels of one colour touch disjoint bins, so
+      // each colour is one accumulator layer written with plain stores
+      std::vector<int> dend, mend;  // last bin taken by each colour
+      auto colour = [](std::vector<int>& ends, int lo, int hi) {
+        for (size_t c = 0; c < ends.size(); ++c)
+          if (ends[c] < lo) { ends[c] = hi; return (int)c; }
+        ends.push_back(hi);
+        return (int)ends.size() - 1;
+      };
+      int flo = (int)N + 1, fhi = -1;  // the group's footprint so far
       while (k < nch) {
         const int lm = pl->bands[k].log2M;
         const int M = 1 << lm;
@@ -161,15 +171,31 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
         if (threads + need_t > kBandThreads) break;
         // one band length per group: every warp of the CTA runs the same code
         if (k > gd.band_begin && lm != pl->bands[gd.band_begin].log2M) break;
-        pl->bands[k].tofs = threads;
-        pl->bands[k].smem_off = smem;
+        BandDesc& d = pl->bands[k];
+        std::vector<int> de = dend, me = mend;
+        const int dp = d.dhi >= 0 ? colour(de, d.dlo, d.dhi) : kNoPhase;
+        const int mp = d.mhi >= 0 ? colour(me, d.mlo, d.mhi) : kNoPhase;
+        const int nlo = foot_hi[k] >= 0 ? std::min(flo, foot_lo[k]) : flo;
+        const int nhi = std::max(fhi, foot_hi[k]);
+        const int acc_n = nhi >= nlo ? nhi - nlo + 1 : 0;
+        const int lay = (int)(de.size() + me.size()) * acc_n;
+        const int need = lm > kMaxTwoPassLog2 ? ((smem + need_s + 1) & ~1) + lay : std::max(smem + need_s, lay);
+        if (k > gd.band_begin && need > kSynSmemBudget) break;
+        if (de.size() >= (size_t)kNoPhase || me.size() >= (size_t)kNoPhase) return SLICQ_EUNSUPPORTED;
+        dend.swap(de);
+        mend.swap(me);
+        flo = nlo;
+        fhi = nhi;
+        d.phases = dp | (mp << 16);
+        d.tofs = threads;
+        d.smem_off = smem;
         threads += need_t;
         smem += need_s;
         ++k;
       }
       gd.band_end = k;
+      gd.nphases = (int)dend.size() | ((int)mend.size() << 16);
       int alo = (int)N + 1, ahi = -1;
-      gd.nmirror = 0;
       int prev_dlo = 0, prev_dhi = -1;
       for (int b = gd.band_begin; b < gd.band_end; ++b) {
         BandDesc& d = pl->bands[b];
@@ -183,11 +209,6 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
           if (d.dlo < prev_dlo || d.dhi < prev_dhi) return SLICQ_EUNSUPPORTED;
           prev_dlo = d.dlo;
           prev_dhi = d.dhi;
-        }
-        if (d.mhi >= 0) {
-          if (gd.nmirror == 0) gd.mirror_off = (int)pl->mirror_list.size();
-          pl->mirror_list.push_back(b);
-          ++gd.nmirror;
         }
       }
       if (ahi < 0) return SLICQ_EINVAL;
@@ -204,6 +225,12 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
         in_a = std::max(in_a, gd.fp_len);
         in_s = std::max(in_s, nb * M);
         tb_max = std::max(tb_max, nb * bufl);
+        // synthesis: the layers overlay the two-pass team buffers (their
+        // values are in registers by then); three-pass teams write their
+        // weighted outputs to the buffers, so the layers follow them
+        const int lay = ((gd.nphases & 0xFFFF) + (gd.nphases >> 16)) * (gd.acc_hi - gd.acc_lo);
+        syn_max = std::max(syn_max, gd.log2M > kMaxTwoPassLog2 ? ((nb * bufl + 1) & ~1) + lay
+                                                               : std::max(nb * bufl, lay));
         smem_p = std::max(smem_p, M + 2 * gd.fp_len + nb * bufl);
         pl->group_cost.push_back(nb * M * (gd.log2M + 4));
       }
@@ -247,6 +274,14 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
     }
     pl->bounds = byg;
   }
+  // boundary g's bins are [ovl_start[g], ovl_start[g + 1]) of a slice's patch row
+  pl->ovl_start.assign(std::max(G, 1), 0);
+  for (int g = 0; g + 1 < G; ++g)
+    pl->ovl_start[g + 1] = pl->ovl_start[g] + (pl->bounds[g].hi - pl->bounds[g].lo);
+  pl->ovl_total = pl->ovl_start[std::max(G, 1) - 1];
+  pl->ovl_bin.clear();
+  for (int g = 0; g + 1 < G; ++g)
+    for (int h = pl->bounds[g].lo; h < pl->bounds[g].hi; ++h) pl->ovl_bin.push_back(h);
   if (pl->groups.front().acc_lo != 0 || pl->groups.back().acc_hi != N + 1) return SLICQ_EINVAL;
   for (int g = 0; g < G; ++g) {
     GroupDesc& gd = pl->groups[g];
@@ -257,10 +292,11 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
   pl->band_in_s = (in_s + 1) & ~1;
   // per-slice band kernels: one team buffer per channel of the group
   pl->band_smem_a = tb_max * (int)sizeof(float2);
-  pl->band_smem_s = tb_max * (int)sizeof(float2);
+  pl->band_smem_s = syn_max * (int)sizeof(float2);
   pl->band_smem_p = smem_p * (int)sizeof(float2);
   if (pl->band_smem_p > 220 * 1024) return SLICQ_EUNSUPPORTED;
-  if (pl->band_smem_a > 220 * 1024 || pl->band_smem_s > 220 * 1024) return SLICQ_EUNSUPPORTED;
+  // synthesis also has 16 KB of static twiddles (227 KB per CTA at most)
+  if (pl->band_smem_a > 220 * 1024 || pl->band_smem_s > 208 * 1024) return SLICQ_EUNSUPPORTED;
 
   // ---- slice FFT geometry: N = P Q, cluster of C CTAs, <= 256 threads each
   const int logN = ilog2_64(N);
@@ -447,7 +483,8 @@ slicq_status build_tables(slicq_plan* pl) {
   const size_t o_groups = take(sizeof(GroupDesc) * pl->G);
   const size_t o_bounds = take(sizeof(BoundaryDesc) * pl->bounds.size());
   const size_t o_tb = take(sizeof(int16_t) * pl->thread_band.size());
-  const size_t o_ml = take(sizeof(int32_t) * std::max<size_t>(pl->mirror_list.size(), 1));
+  const size_t o_ovl = take(sizeof(int32_t) * pl->ovl_start.size());
+  const size_t o_ovlb = take(sizeof(int32_t) * std::max<size_t>(pl->ovl_bin.size(), 1));
   const size_t o_ga = take(sizeof(float) * (pl->win_total + 32));  // + padding
   const size_t o_gs = take(sizeof(float) * (pl->win_total + 32));  // + padding
   const size_t o_gadj = take(sizeof(float) * (pl->win_total + 32));  // + padding
@@ -482,7 +519,8 @@ slicq_status build_tables(slicq_plan* pl) {
   pl->d_groups = (GroupDesc*)(base + o_groups);
   pl->d_bounds = (BoundaryDesc*)(base + o_bounds);
   pl->d_thread_band = (int16_t*)(base + o_tb);
-  pl->d_mirror_list = (int32_t*)(base + o_ml);
+  pl->d_ovl_start = (int32_t*)(base + o_ovl);
+  pl->d_ovl_bin = (int32_t*)(base + o_ovlb);
   pl->d_ga = (float*)(base + o_ga);
   pl->d_gs = (float*)(base + o_gs);
   pl->d_gadj = (float*)(base + o_gadj);
@@ -512,8 +550,11 @@ slicq_status build_tables(slicq_plan* pl) {
   if (e == cudaSuccess)
     e = cudaMemcpy(pl->d_thread_band, pl->thread_band.data(),
                    sizeof(int16_t) * pl->thread_band.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && !pl->mirror_list.empty())
-    e = cudaMemcpy(pl->d_mirror_list, pl->mirror_list.data(), sizeof(int32_t) * pl->mirror_list.size(),
+  if (e == cudaSuccess)
+    e = cudaMemcpy(pl->d_ovl_start, pl->ovl_start.data(), sizeof(int32_t) * pl->ovl_start.size(),
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !pl->ovl_bin.empty())
+    e = cudaMemcpy(pl->d_ovl_bin, pl->ovl_bin.data(), sizeof(int32_t) * pl->ovl_bin.size(),
                    cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(pl->d_cta_map, cta_map.data(), sizeof(int2) * cta_map.size(), cudaMemcpyHostToDevice);

@@ -207,7 +207,8 @@ class SliCQPlan:
                "slicq_plan_table")
         return buf[: n.value].copy()
 
-    KERNEL_NAMES = ("slice_forward", "band_analysis", "band_synthesis", "slice_inverse")
+    KERNEL_NAMES = ("slice_forward", "band_analysis", "band_synthesis", "slice_inverse",
+                    "band_boundary")
 
     def trace(self, enable: bool = True):
         """Start (or stop) recording CUDA events around every kernel launch."""
