@@ -27,7 +27,6 @@ namespace {
 // Pass-2 twiddles of every band length M = 2^LOGM (LOGM = 4..10): entry
 // (M - 16) + r R1 + j holds exp(-2 pi i j r / M), r < R2, j < R1, so that the
 // threads of a team (consecutive j) read consecutive words.
-constexpr int kTwSmall = 2032;
 
 struct BandArgs {
   const BandDesc* __restrict__ bands;
@@ -37,7 +36,7 @@ struct BandArgs {
   const int32_t* __restrict__ ovl_start;    // [G] boundary offsets in a patch row
   const int32_t* __restrict__ ovl_bin;      // [ovl_total] bin of each patch-row entry
   const float* __restrict__ win;     // window table of this launch
-  const float2* __restrict__ twband; // pass-2 twiddle tables, kTwSmall entries
+  const float2* __restrict__ twband; // pass-2 twiddle tables of lengths 16..1024 (2032 entries)
   const float2* __restrict__ tw4096; // exp(-2 pi i t / 4096), t < 4096 (three-pass lengths)
   float2* spec;                      // [slice][spec_stride]
   int64_t slice_base;                // first slice of this launch (per-slice kernels)
@@ -48,26 +47,17 @@ struct BandArgs {
   float2* patch;                     // [slice][2][ovl_total]
   int ovl_total;
   int N;
-};
-
-__device__ __forceinline__ void load_twiddles(const BandArgs& a, float2* s_tw) {
-  for (int i = threadIdx.x; i < kTwSmall; i += blockDim.x) s_tw[i] = __ldg(a.twband + i);
-}
-
-// exp(SIGN 2 pi i j r / 2^LOGM) from the shared pass-2 tables
-template <int LOGM, int SIGN>
-struct BandTw {
-  const float2* s_tw;
-  __device__ __forceinline__ float2 operator()(int j, int r) const {
-    const float2 w = s_tw[((1 << LOGM) - 16) + r * Team<LOGM>::R1 + j];
-    return SIGN < 0 ? w : c_conj(w);
-  }
+  long long* cycles;                 // optional: SM clocks of each CTA (plan calibration)
 };
 
 // --------------------------------------------------------------- cp.async ---
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int PENDING>
@@ -203,6 +193,7 @@ __global__ void __launch_bounds__(kBandThreads, 1) band_analysis_persistent_kern
   const GroupDesc gd = a.groups[gl.x];
   const int lanes = lanes_of[gl.x];
   const int64_t total = a.total;
+  const long long t0 = clock64();
   switch (gd.log2M) {
     case 4: analysis_persistent<4>(a, gd, gl.y, lanes, total, sm); break;
     case 5: analysis_persistent<5>(a, gd, gl.y, lanes, total, sm); break;
@@ -214,197 +205,278 @@ __global__ void __launch_bounds__(kBandThreads, 1) band_analysis_persistent_kern
     case 11: analysis_persistent<11>(a, gd, gl.y, lanes, total, sm); break;
     case 12: analysis_persistent<12>(a, gd, gl.y, lanes, total, sm); break;
   }
+  if (a.cycles) {
+    __syncthreads();
+    if (threadIdx.x == 0) a.cycles[blockIdx.x] = clock64() - t0;
+  }
 }
 
 // ----------------------------------------------------------- synthesis ---
-
-template <int LOGM>
-__device__ __forceinline__ void synthesis_pass1(int tt, const float2* __restrict__ c, float2* buf) {
-  team_pass1<LOGM, -1>(tt, buf, [&](int idx) { return __ldcs(c + idx); });
-}
-
-template <int LOGM>
-__device__ __forceinline__ void synthesis_pass2(int tt, const float2* s_tw, const float2* buf,
-                                                float2* res) {
-  team_pass2<LOGM, -1>(tt, buf, BandTw<LOGM, -1>{s_tw}, res);
-}
-
-// Stores the thread's values Y[idx] w g~[o] (o = idx - j0 mod M < |J_k|) to
-// the channel's layers: layer[dl][j] for the direct bins, layer[ml][2N - j]
-// (conjugated) for the mirrored ones.  layer(l) points at layer l, indexed by
-// bin.  The window loads are unconditional (index clamped) so that they are
-// all in flight together.
-template <int LOGM>
-__device__ __forceinline__ void store_held(const BandArgs& a, const BandDesc& bd, int tt,
-                                           const float2* res, float2* dl, float2* ml) {
-  using T = Team<LOGM>;
-  constexpr int M = 1 << LOGM;
-  const float* __restrict__ g = a.win + bd.win_off;
-  const int twoN = 2 * a.N;
-#pragma unroll
-  for (int i = 0; i < T::J2; ++i)
-#pragma unroll
-    for (int r = 0; r < T::R2; ++r) {
-      const int o = (team_out_index<LOGM>(tt, i, r) - bd.j0) & (M - 1);
-      const bool in = o < bd.len;
-      const float2 y = c_scale(res[i * T::R2 + r], __ldg(g + (in ? o : 0)));
-      int b = bd.j0 + o;
-      if (b >= twoN) b -= twoN;
-      if (in && b <= a.N) dl[b] = y;
-      if (in && (b == 0 || b >= a.N)) ml[b == 0 ? 0 : twoN - b] = c_conj(y);
-    }
-}
-
-__device__ __forceinline__ void store_held_m(int log2M, const BandArgs& a, const BandDesc& bd, int tt,
-                                             const float2* res, float2* dl, float2* ml) {
-  switch (log2M) {
-    case 4: store_held<4>(a, bd, tt, res, dl, ml); break;
-    case 5: store_held<5>(a, bd, tt, res, dl, ml); break;
-    case 6: store_held<6>(a, bd, tt, res, dl, ml); break;
-    case 7: store_held<7>(a, bd, tt, res, dl, ml); break;
-    case 8: store_held<8>(a, bd, tt, res, dl, ml); break;
-    case 9: store_held<9>(a, bd, tt, res, dl, ml); break;
-    case 10: store_held<10>(a, bd, tt, res, dl, ml); break;
-  }
-}
+// Persistent form: CTA c keeps group cta_group[c] and walks the slices
+// s = lane, lane + lanes, ...  Shared memory: [pass-2 twiddles (two-pass
+// lengths)][team buffers][accumulator layers].  Per slice: pass 1, pass 2
+// (while the next slice's coefficients load into registers), weighted
+// values to the layers, then every bin of the group to the spectrum or a
+// patch row; the write-out zeroes the layers for the next slice.
 
 // Zeroes n complex values at p (p 16-byte aligned) with 16-byte stores.
 __device__ __forceinline__ void zero_layers(float2* p, int n) {
   float4* q = reinterpret_cast<float4*>(p);
   const int n4 = n >> 1;
   const float4 z = make_float4(0.f, 0.f, 0.f, 0.f);
-  int i = threadIdx.x;
-  for (; i + 3 * kBandThreads < n4; i += 4 * kBandThreads) {
-    q[i] = z;
-    q[i + kBandThreads] = z;
-    q[i + 2 * kBandThreads] = z;
-    q[i + 3 * kBandThreads] = z;
-  }
-  for (; i < n4; i += kBandThreads) q[i] = z;
+  for (int i = threadIdx.x; i < n4; i += kBandThreads) q[i] = z;
   if ((n & 1) && threadIdx.x == 0) p[n - 1] = make_float2(0.f, 0.f);
 }
 
-// Bins [acc_lo, acc_hi): the sum of the NL layers (fixed order) to the
-// spectrum, or to a patch row for bins shared with a neighbouring group.
+// Where slice s's bins of the group go: the spectrum row, or the patch rows
+// for bins shared with a neighbouring group (side 0: the lower group of a
+// boundary, side 1: the upper one).
+struct BinSink {
+  float2* spec;
+  float2* patch_l;
+  float2* patch_r;
+  int ex_lo, ex_hi;
+  __device__ __forceinline__ BinSink(const BandArgs& a, const GroupDesc& gd, int64_t s) {
+    spec = a.spec + s * a.spec_stride;
+    float2* row = a.patch + s * 2 * (int64_t)a.ovl_total;
+    patch_l = gd.left_bd >= 0 ? row + a.ovl_total + a.ovl_start[gd.left_bd] - gd.acc_lo : nullptr;
+    patch_r = gd.right_bd >= 0 ? row + a.ovl_start[gd.right_bd] - gd.ex_hi : nullptr;
+    ex_lo = gd.ex_lo;
+    ex_hi = gd.ex_hi;
+  }
+  __device__ __forceinline__ void put(int h, float2 v) const {
+    if (h < ex_lo) patch_l[h] = v;
+    else if (h >= ex_hi) patch_r[h] = v;
+    else spec[h] = v;
+  }
+};
+
+// Bins [acc_lo, acc_hi): the sum of the NL layers in layer order (NL = 0:
+// nl layers), zeroing them for the next slice.
 template <int NL>
-__device__ __forceinline__ void write_bins(const GroupDesc& gd, const float2* lay, int nl, int acc_n,
-                                           float2* spec, float2* patch_l, float2* patch_r) {
+__device__ __forceinline__ void write_bins(const GroupDesc& gd, float2* lay, int nl, int acc_n,
+                                           const BinSink& out) {
+  const float2 z = make_float2(0.f, 0.f);
   for (int h = gd.acc_lo + (int)threadIdx.x; h < gd.acc_hi; h += kBandThreads) {
-    const float2* p = lay + (h - gd.acc_lo);
+    float2* p = lay + (h - gd.acc_lo);
     float2 v = p[0];
+    p[0] = z;
     if (NL > 0) {
 #pragma unroll
-      for (int l = 1; l < NL; ++l) v = c_add(v, p[l * acc_n]);
+      for (int l = 1; l < NL; ++l) {
+        v = c_add(v, p[l * acc_n]);
+        p[l * acc_n] = z;
+      }
     } else {
-      for (int l = 1; l < nl; ++l) v = c_add(v, p[l * acc_n]);
+      for (int l = 1; l < nl; ++l) {
+        v = c_add(v, p[l * acc_n]);
+        p[l * acc_n] = z;
+      }
     }
-    if (h < gd.ex_lo) patch_l[h] = v;
-    else if (h >= gd.ex_hi) patch_r[h] = v;
-    else spec[h] = v;
+    out.put(h, v);
   }
 }
 
-__global__ void __launch_bounds__(kBandThreads, 2) band_synthesis_kernel(BandArgs a) {
-  extern __shared__ __align__(16) float2 sm[];
-  __shared__ float2 s_tw[kTwSmall];
-  // slices vary fastest: CTAs resident together mostly run one group's code
-  const int g = blockIdx.y;
-  const int64_t s = a.slice_base + blockIdx.x;
-  const int t = threadIdx.x;
-  const int k = a.thread_band[g * kBandThreads + t];
-  const GroupDesc gd = a.groups[g];
-  const int nb = gd.band_end - gd.band_begin;
-  BandDesc bd{};
-  if (k >= 0) bd = a.bands[k];
-  const int tt = t - bd.tofs;
-  const int M = 1 << gd.log2M;
-  const bool three = gd.log2M > kMaxTwoPassLog2;
-  // accumulator layers over bins [acc_lo, acc_hi): direct colours first, then
-  // the mirrored ones.  Two-pass teams hold their values in registers when
-  // the layers are filled, so the layers overlay their buffers.
-  const int acc_n = gd.acc_hi - gd.acc_lo;
-  const int nd = gd.nphases & 0xFFFF;
-  const int nl = nd + (gd.nphases >> 16);
-  float2* lay = three ? sm + ((nb * (M + 1) + 1) & ~1) : sm;  // 16-byte aligned
-  // this channel's layers, indexed by bin (a channel without direct or
-  // mirrored bins never writes the corresponding one)
-  const int dli = bd.phases & 0xFFFF, mli = bd.phases >> 16;
-  float2* dl = lay + (dli == kNoPhase ? 0 : dli) * acc_n - gd.acc_lo;
-  float2* ml = lay + (mli == kNoPhase ? 0 : nd + mli) * acc_n - gd.acc_lo;
-  float2* buf = sm + bd.smem_off;
-  const float2* c = a.coef + s * a.cps + bd.coef_off;
+__device__ __forceinline__ void write_bins_n(const GroupDesc& gd, float2* lay, int nl, int acc_n,
+                                             const BinSink& out) {
+  switch (nl) {
+    case 1: write_bins<1>(gd, lay, nl, acc_n, out); break;
+    case 2: write_bins<2>(gd, lay, nl, acc_n, out); break;
+    case 3: write_bins<3>(gd, lay, nl, acc_n, out); break;
+    case 4: write_bins<4>(gd, lay, nl, acc_n, out); break;
+    default: write_bins<0>(gd, lay, nl, acc_n, out); break;
+  }
+}
 
-  if (three) {
-    zero_layers(lay, nl * acc_n);
-    // the team spans warps; its last pass writes Y w g~ at the support offsets
-    const float* __restrict__ gw = a.win + bd.win_off;
+// The channel's two layers, indexed by bin: direct colours come first, then
+// the mirrored ones (a channel without direct or mirrored bins never writes
+// the corresponding one).
+struct ChannelLayers {
+  float2* dl;
+  float2* ml;
+  __device__ __forceinline__ ChannelLayers(const BandDesc& bd, const GroupDesc& gd, float2* lay, int acc_n) {
+    const int nd = gd.nphases & 0xFFFF;
+    const int dli = bd.phases & 0xFFFF, mli = bd.phases >> 16;
+    dl = lay + (dli == kNoPhase ? 0 : dli) * acc_n - gd.acc_lo;
+    ml = lay + (mli == kNoPhase ? 0 : nd + mli) * acc_n - gd.acc_lo;
+  }
+  // value y of support bin b (0 <= b < 2N) to its direct and mirrored bins
+  __device__ __forceinline__ void put(int b, float2 y, int N, int twoN) const {
+    if (b <= N) dl[b] = y;
+    if (b == 0 || b >= N) ml[b == 0 ? 0 : twoN - b] = c_conj(y);
+  }
+};
+
+template <int LOGM>
+__device__ void synthesis_two_pass(const BandArgs& a, const GroupDesc& gd, int k, int lane, int lanes,
+                                   int64_t total, float2* sm) {
+  using T = Team<LOGM>;
+  constexpr int M = 1 << LOGM;
+  const int t = threadIdx.x;
+  const int nb = gd.band_end - gd.band_begin;
+  const bool active = k >= 0;
+  BandDesc bd{};
+  if (active) bd = a.bands[k];
+  const int twoN = 2 * a.N;
+  const int acc_n = gd.acc_hi - gd.acc_lo;
+  const int nl = (gd.nphases & 0xFFFF) + (gd.nphases >> 16);
+  const int lay_off = (M + nb * T::BUF + 1) & ~1;
+  float2* lay = sm + lay_off;
+
+  for (int i = t; i < M; i += kBandThreads) sm[i] = __ldg(a.twband + (M - 16) + i);
+  zero_layers(lay, nl * acc_n);
+  // window values of the held outputs: the same in every slice (registers)
+  float w[T::HELD];
+  {
+    const float* __restrict__ g = a.win + bd.win_off;
+    const int tt = t - bd.tofs;
+#pragma unroll
+    for (int i = 0; i < T::J2; ++i)
+#pragma unroll
+      for (int r = 0; r < T::R2; ++r) {
+        const int o = (team_out_index<LOGM>(tt, i, r) - bd.j0) & (M - 1);
+        w[i * T::R2 + r] = active && o < bd.len ? __ldg(g + o) : 0.f;
+      }
+  }
+  // The loop body derives every address from these integers again in each
+  // slice: passed through an empty asm, they look new to the compiler, which
+  // would otherwise compute all of them once before the loop and keep them
+  // live in registers across it.
+  struct Opaque {
+    int tt, j0, len, buf, dl, ml;
+  };
+  const ChannelLayers cl0(bd, gd, lay, acc_n);
+  const Opaque op0{t - bd.tofs, bd.j0, bd.len, M + bd.smem_off, (int)(cl0.dl - sm), (int)(cl0.ml - sm)};
+  auto opaque = [&]() {
+    Opaque o = op0;
+    asm volatile("" : "+r"(o.tt), "+r"(o.j0), "+r"(o.len), "+r"(o.buf), "+r"(o.dl), "+r"(o.ml));
+    return o;
+  };
+  // slice s's coefficients into the team buffer at their natural positions;
+  // each thread copies exactly the elements it reads in pass 1
+  auto fetch = [&](const Opaque& q, int64_t s) {
+    const float2* c = a.coef + s * a.cps + bd.coef_off;
+    float2* buf = sm + q.buf;
+#pragma unroll
+    for (int i = 0; i < T::J1; ++i)
+#pragma unroll
+      for (int r = 0; r < T::R1; ++r) {
+        const int idx = q.tt + T::TT * i + r * T::R2;
+        cp_async8(buf + idx, c + idx);
+      }
+  };
+  int64_t s = lane;
+  if (active && s < total) fetch(opaque(), s);
+  cp_async_commit();
+  __syncthreads();  // twiddles staged, layers zeroed
+  for (; s < total; s += lanes) {
+    const Opaque q = opaque();
+    float2* buf = sm + q.buf;
+    float2 res[T::HELD];
+    float2 v[T::J1][T::R1];
+    cp_async_wait<0>();  // this thread's copies have landed
+    if (active) {
+#pragma unroll
+      for (int i = 0; i < T::J1; ++i)
+#pragma unroll
+        for (int r = 0; r < T::R1; ++r) v[i][r] = buf[q.tt + T::TT * i + r * T::R2];
+    }
+    __syncwarp();  // the team has read its inputs: pass 1 overwrites them
+    if (active) team_pass1_regs<LOGM, -1>(q.tt, buf, v);
+    __syncwarp();
+    if (active) team_pass2<LOGM, -1>(q.tt, buf, [&](int j, int r) { return sm[r * T::R1 + j]; }, res);
+    __syncwarp();  // the team has read its buffer: refill it with the next slice
+    if (active && s + lanes < total) fetch(q, s + lanes);
+    cp_async_commit();
+    __syncthreads();  // the previous slice's write-out has zeroed the layers
+    if (active) {
+      float2* dl = sm + q.dl;
+      float2* ml = sm + q.ml;
+#pragma unroll
+      for (int i = 0; i < T::J2; ++i)
+#pragma unroll
+        for (int r = 0; r < T::R2; ++r) {
+          const int o = (team_out_index<LOGM>(q.tt, i, r) - q.j0) & (M - 1);
+          int b = q.j0 + o;
+          if (b >= twoN) b -= twoN;
+          if (o < q.len) {
+            const float2 y = c_scale(res[i * T::R2 + r], w[i * T::R2 + r]);
+            if (b <= a.N) dl[b] = y;
+            if (b == 0 || b >= a.N) ml[b == 0 ? 0 : twoN - b] = c_conj(y);
+          }
+        }
+    }
+    __syncthreads();
+    write_bins_n(gd, lay, nl, acc_n, BinSink(a, gd, s));
+  }
+  cp_async_wait<0>();
+}
+
+// Three-pass lengths (2048, 4096): the team spans warps and its last pass
+// writes Y w g~ at the support offsets of its buffer; windows and twiddles
+// come from global memory (L1-resident).
+template <int LOGM>
+__device__ void synthesis_three_pass(const BandArgs& a, const GroupDesc& gd, int k, int lane, int lanes,
+                                     int64_t total, float2* sm) {
+  constexpr int M = 1 << LOGM;
+  const int t = threadIdx.x;
+  const int nb = gd.band_end - gd.band_begin;
+  const bool active = k >= 0;
+  BandDesc bd{};
+  if (active) bd = a.bands[k];
+  const int tt = t - bd.tofs;
+  const int twoN = 2 * a.N;
+  const int acc_n = gd.acc_hi - gd.acc_lo;
+  const int nl = (gd.nphases & 0xFFFF) + (gd.nphases >> 16);
+  float2* buf = sm + bd.smem_off;
+  float2* lay = sm + ((nb * (M + 1) + 1) & ~1);
+  const ChannelLayers cl(bd, gd, lay, acc_n);
+  const float* __restrict__ gw = a.win + bd.win_off;
+  zero_layers(lay, nl * acc_n);  // the transform's first barrier orders this
+  for (int64_t s = lane; s < total; s += lanes) {
+    const float2* c = a.coef + s * a.cps + bd.coef_off;
     auto in = [&](int idx) { return __ldcs(c + idx); };
     auto contrib = [&](int idx, float2 v) {
       const int o = (idx - bd.j0) & (M - 1);
       if (o < bd.len) buf[o] = c_scale(v, __ldg(gw + o));
     };
-    if (gd.log2M == 11) band_three_pass<11, -1>(k >= 0, tt, buf, a.tw4096, in, contrib);
-    else band_three_pass<12, -1>(k >= 0, tt, buf, a.tw4096, in, contrib);
-    __syncthreads();
-    if (k >= 0) {
-      const int twoN = 2 * a.N;
+    band_three_pass<LOGM, -1>(active, tt, buf, a.tw4096, in, contrib);
+    __syncthreads();  // weighted values in the buffers; previous write-out done
+    if (active) {
       for (int o = tt; o < bd.len; o += M / kPerThread) {
         int b = bd.j0 + o;
         if (b >= twoN) b -= twoN;
-        const float2 y = buf[o];
-        if (b <= a.N) dl[b] = y;
-        if (b == 0 || b >= a.N) ml[b == 0 ? 0 : twoN - b] = c_conj(y);
+        cl.put(b, buf[o], a.N, twoN);
       }
     }
-  } else {
-    // pass-2 twiddles of this group's length only (pass 1 does not need them:
-    // the barrier after it covers the staging)
-    for (int i = t; i < M; i += blockDim.x) s_tw[(M - 16) + i] = __ldg(a.twband + (M - 16) + i);
-    if (k >= 0) {
-      switch (bd.log2M) {
-        case 4: synthesis_pass1<4>(tt, c, buf); break;
-        case 5: synthesis_pass1<5>(tt, c, buf); break;
-        case 6: synthesis_pass1<6>(tt, c, buf); break;
-        case 7: synthesis_pass1<7>(tt, c, buf); break;
-        case 8: synthesis_pass1<8>(tt, c, buf); break;
-        case 9: synthesis_pass1<9>(tt, c, buf); break;
-        case 10: synthesis_pass1<10>(tt, c, buf); break;
-      }
-    }
-    __syncthreads();  // twiddles staged; pass-1 outputs in the team buffers
-    float2 res[kPerThread];
-    if (k >= 0) {
-      switch (bd.log2M) {
-        case 4: synthesis_pass2<4>(tt, s_tw, buf, res); break;
-        case 5: synthesis_pass2<5>(tt, s_tw, buf, res); break;
-        case 6: synthesis_pass2<6>(tt, s_tw, buf, res); break;
-        case 7: synthesis_pass2<7>(tt, s_tw, buf, res); break;
-        case 8: synthesis_pass2<8>(tt, s_tw, buf, res); break;
-        case 9: synthesis_pass2<9>(tt, s_tw, buf, res); break;
-        case 10: synthesis_pass2<10>(tt, s_tw, buf, res); break;
-      }
-    }
-    __syncthreads();  // every team has read its buffer
-    zero_layers(lay, nl * acc_n);
     __syncthreads();
-    if (k >= 0) store_held_m(gd.log2M, a, bd, tt, res, dl, ml);
+    write_bins_n(gd, lay, nl, acc_n, BinSink(a, gd, s));
   }
-  __syncthreads();
+}
 
-  // bins of this group alone to the spectrum, shared bins to the patch rows
-  // (side 0: the lower group of a boundary, side 1: the upper one)
-  float2* spec = a.spec + s * a.spec_stride;
-  float2* row = a.patch + s * 2 * (int64_t)a.ovl_total;
-  float2* patch_l = nullptr;
-  float2* patch_r = nullptr;
-  if (gd.left_bd >= 0) patch_l = row + a.ovl_total + a.ovl_start[gd.left_bd] - gd.acc_lo;
-  if (gd.right_bd >= 0) patch_r = row + a.ovl_start[gd.right_bd] - gd.ex_hi;
-  switch (nl) {
-    case 1: write_bins<1>(gd, lay, nl, acc_n, spec, patch_l, patch_r); break;
-    case 2: write_bins<2>(gd, lay, nl, acc_n, spec, patch_l, patch_r); break;
-    case 3: write_bins<3>(gd, lay, nl, acc_n, spec, patch_l, patch_r); break;
-    case 4: write_bins<4>(gd, lay, nl, acc_n, spec, patch_l, patch_r); break;
-    default: write_bins<0>(gd, lay, nl, acc_n, spec, patch_l, patch_r); break;
+__global__ void __launch_bounds__(kBandThreads, 1) band_synthesis_persistent_kernel(
+    BandArgs a, const int2* __restrict__ cta_map, const int* __restrict__ lanes_of) {
+  extern __shared__ __align__(16) float2 sm[];
+  const int2 gl = cta_map[blockIdx.x];  // (group, lane)
+  const GroupDesc gd = a.groups[gl.x];
+  const int lanes = lanes_of[gl.x];
+  const int k = a.thread_band[gl.x * kBandThreads + threadIdx.x];
+  const int64_t total = a.total;
+  const long long t0 = clock64();
+  switch (gd.log2M) {
+    case 4: synthesis_two_pass<4>(a, gd, k, gl.y, lanes, total, sm); break;
+    case 5: synthesis_two_pass<5>(a, gd, k, gl.y, lanes, total, sm); break;
+    case 6: synthesis_two_pass<6>(a, gd, k, gl.y, lanes, total, sm); break;
+    case 7: synthesis_two_pass<7>(a, gd, k, gl.y, lanes, total, sm); break;
+    case 8: synthesis_two_pass<8>(a, gd, k, gl.y, lanes, total, sm); break;
+    case 9: synthesis_two_pass<9>(a, gd, k, gl.y, lanes, total, sm); break;
+    case 10: synthesis_two_pass<10>(a, gd, k, gl.y, lanes, total, sm); break;
+    case 11: synthesis_three_pass<11>(a, gd, k, gl.y, lanes, total, sm); break;
+    case 12: synthesis_three_pass<12>(a, gd, k, gl.y, lanes, total, sm); break;
+  }
+  if (a.cycles) {
+    __syncthreads();
+    if (threadIdx.x == 0) a.cycles[blockIdx.x] = clock64() - t0;
   }
 }
 
@@ -455,33 +527,32 @@ BandArgs make_args(const slicq_plan* pl, const Workspace& ws, const float* win) 
 }  // namespace
 
 cudaError_t launch_band_analysis(const slicq_plan* pl, const Workspace& ws, int64_t batch,
-                                 float2* coef, cudaStream_t st) {
+                                 float2* coef, cudaStream_t st, long long* cycles) {
   BandArgs a = make_args(pl, ws, pl->d_ga);
   a.coef = coef;
+  a.cycles = cycles;
   a.total = batch * ws.S;
   cudaError_t e = cudaFuncSetAttribute(band_analysis_persistent_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, pl->band_smem_p);
   if (e != cudaSuccess) return e;
   band_analysis_persistent_kernel<<<pl->n_cta_a, kBandThreads, pl->band_smem_p, st>>>(
-      a, pl->d_cta_map, pl->d_lanes);
+      a, pl->d_cta_map_a, pl->d_lanes_a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_band_synthesis(const slicq_plan* pl, const float2* coef, int64_t batch,
-                                  SynthKind kind, const Workspace& ws, cudaStream_t st) {
+                                  SynthKind kind, const Workspace& ws, cudaStream_t st,
+                                  long long* cycles) {
   BandArgs a = make_args(pl, ws, kind == kSynthInverse ? pl->d_gs : pl->d_gadj);
   a.coef = const_cast<float2*>(coef);
-  cudaError_t e = cudaFuncSetAttribute(band_synthesis_kernel,
+  a.cycles = cycles;
+  a.total = batch * ws.S;
+  cudaError_t e = cudaFuncSetAttribute(band_synthesis_persistent_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, pl->band_smem_s);
   if (e != cudaSuccess) return e;
-  const int64_t total = batch * ws.S;
-  for (int64_t s0 = 0; s0 < total; s0 += kMaxGridY) {
-    a.slice_base = s0;
-    dim3 grid((unsigned)(total - s0 < kMaxGridY ? total - s0 : kMaxGridY), pl->G);
-    band_synthesis_kernel<<<grid, kBandThreads, pl->band_smem_s, st>>>(a);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  band_synthesis_persistent_kernel<<<pl->n_cta_s, kBandThreads, pl->band_smem_s, st>>>(
+      a, pl->d_cta_map_s, pl->d_lanes_s);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_band_boundaries(const slicq_plan* pl, int64_t batch, const Workspace& ws,

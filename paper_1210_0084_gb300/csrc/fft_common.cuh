@@ -141,6 +141,21 @@ struct Team {
   __device__ __forceinline__ static int pad2(int j, int r) { return j + r * (R1 + 1); }
 };
 
+// Pass 1 on values already in registers: v[i][r] is input element
+// tt + TT i + r R2 (overwritten by the transform).
+template <int LOGL, int SIGN>
+__device__ __forceinline__ void team_pass1_regs(int tt, float2* __restrict__ buf,
+                                                float2 (&v)[Team<LOGL>::J1][Team<LOGL>::R1]) {
+  using T = Team<LOGL>;
+#pragma unroll
+  for (int i = 0; i < T::J1; ++i) {
+    const int j = tt + T::TT * i;
+    dft_reg<T::R1, SIGN>(v[i]);
+#pragma unroll
+    for (int r = 0; r < T::R1; ++r) buf[T::pad1(j, r)] = v[i][r];
+  }
+}
+
 // Pass 1: LOAD(idx) gives input element idx (0 <= idx < L).  All of the
 // thread's loads are issued before the first DFT so that they are in flight
 // together.
@@ -152,13 +167,7 @@ __device__ __forceinline__ void team_pass1(int tt, float2* __restrict__ buf, Loa
   for (int i = 0; i < T::J1; ++i)
 #pragma unroll
     for (int r = 0; r < T::R1; ++r) v[i][r] = load(tt + T::TT * i + r * T::R2);
-#pragma unroll
-  for (int i = 0; i < T::J1; ++i) {
-    const int j = tt + T::TT * i;
-    dft_reg<T::R1, SIGN>(v[i]);
-#pragma unroll
-    for (int r = 0; r < T::R1; ++r) buf[T::pad1(j, r)] = v[i][r];
-  }
+  team_pass1_regs<LOGL, SIGN>(tt, buf, v);
 }
 
 // Pass 2 (read half): twiddled, transformed values into res[i * R2 + r] for

@@ -20,8 +20,9 @@ constexpr int kMinBandLog2 = 4;   // M_k >= 16
 constexpr int kSliceMaxThreads = 256;  // slice kernels: N / (32 C) <= 256
 constexpr int64_t kMaxGridY = 65535;
 // shared memory (complex values) a band group's synthesis may use for its
-// team buffers and accumulator layers; a group closes before exceeding it
-constexpr int kSynSmemBudget = 12288;
+// twiddles, team buffers and accumulator layers; a group closes before
+// exceeding it
+constexpr int kSynSmemBudget = 26624;
 
 // One kept channel k = 0..K+1 on the slice circle Z_{2N} (Sec. 3).
 struct BandDesc {
@@ -90,7 +91,8 @@ struct slicq_plan {
   int num_sms = 152;      // SMs of the plan's device (grid sizing)
   int band_smem_p = 0;    // dynamic shared memory of the persistent band analysis (bytes)
   int n_cta_a = 0;        // CTAs of the persistent band analysis
-  std::vector<int> group_cost;  // relative work of one slice of each group
+  int n_cta_s = 0;        // CTAs of the persistent band synthesis
+  std::vector<double> cost_a, cost_s;  // estimated cycles per slice of each group
   int slice_smem = 0;     // dynamic shared memory of the slice kernels (bytes)
   int slice_tw_off = 0;   // float2 offset of the twiddle tables in that memory
   int tw_lb = 0;          // log2 of the fine twiddle table length
@@ -118,8 +120,10 @@ struct slicq_plan {
   float* d_gadj = nullptr;  // g_k / (2 sqrt(2N))
   float* d_hw = nullptr;    // Tukey transition, M + 1 values
   float* d_h0 = nullptr;    // h_0 over one slice, 2N values
-  int2* d_cta_map = nullptr;  // persistent band analysis: CTA -> (group, lane)
-  int* d_lanes = nullptr;     // lanes (CTAs) per group
+  int2* d_cta_map_a = nullptr;  // persistent band analysis: CTA -> (group, lane)
+  int* d_lanes_a = nullptr;     // its lanes (CTAs) per group
+  int2* d_cta_map_s = nullptr;  // persistent band synthesis: CTA -> (group, lane)
+  int* d_lanes_s = nullptr;     // its lanes (CTAs) per group
   float2* d_tw_lo = nullptr;  // exp(-2 pi i t / 2N), t < 2^tw_lb
   float2* d_tw_hi = nullptr;  // exp(-2 pi i (t << tw_lb) / 2N)
   float2* d_twband = nullptr; // band pass-2 twiddles, per length, [r][j] layout
@@ -162,11 +166,15 @@ size_t workspace_layout(const slicq_plan* pl, int64_t n_samples, int64_t batch,
 cudaError_t launch_slice_forward(const slicq_plan* pl, const float* f,
                                  int64_t n, int64_t batch, const Workspace& ws,
                                  cudaStream_t st, const RowDesc* rows = nullptr);
+// `cycles` (optional, one per CTA): SM clocks each CTA of the persistent
+// band kernel took, for the plan's lane calibration.
 cudaError_t launch_band_analysis(const slicq_plan* pl, const Workspace& ws,
-                                 int64_t batch, float2* coef, cudaStream_t st);
+                                 int64_t batch, float2* coef, cudaStream_t st,
+                                 long long* cycles = nullptr);
 cudaError_t launch_band_synthesis(const slicq_plan* pl, const float2* coef,
                                   int64_t batch, SynthKind kind,
-                                  const Workspace& ws, cudaStream_t st);
+                                  const Workspace& ws, cudaStream_t st,
+                                  long long* cycles = nullptr);
 // Adds the two partial sums of the bins shared by neighbouring band groups
 // (after launch_band_synthesis, before launch_slice_inverse).
 cudaError_t launch_band_boundaries(const slicq_plan* pl, int64_t batch, const Workspace& ws,

@@ -144,7 +144,8 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
   pl->groups.clear();
   pl->thread_band.clear();
   int in_a = 0, in_s = 0, tb_max = 0, smem_p = 0, syn_max = 0;  // complex values
-  pl->group_cost.clear();
+  pl->cost_a.clear();
+  pl->cost_s.clear();
   {
     int k = 0;
     while (k < nch) {
@@ -179,7 +180,8 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
         const int nhi = std::max(fhi, foot_hi[k]);
         const int acc_n = nhi >= nlo ? nhi - nlo + 1 : 0;
         const int lay = (int)(de.size() + me.size()) * acc_n;
-        const int need = lm > kMaxTwoPassLog2 ? ((smem + need_s + 1) & ~1) + lay : std::max(smem + need_s, lay);
+        // synthesis shared memory: [pass-2 twiddles][team buffers][layers]
+        const int need = ((lm > kMaxTwoPassLog2 ? 0 : M) + smem + need_s + 1 & ~1) + lay;
         if (k > gd.band_begin && need > kSynSmemBudget) break;
         if (de.size() >= (size_t)kNoPhase || me.size() >= (size_t)kNoPhase) return SLICQ_EUNSUPPORTED;
         dend.swap(de);
@@ -225,14 +227,23 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
         in_a = std::max(in_a, gd.fp_len);
         in_s = std::max(in_s, nb * M);
         tb_max = std::max(tb_max, nb * bufl);
-        // synthesis: the layers overlay the two-pass team buffers (their
-        // values are in registers by then); three-pass teams write their
-        // weighted outputs to the buffers, so the layers follow them
+        // synthesis: [pass-2 twiddles (two-pass lengths)][team buffers][layers]
         const int lay = ((gd.nphases & 0xFFFF) + (gd.nphases >> 16)) * (gd.acc_hi - gd.acc_lo);
-        syn_max = std::max(syn_max, gd.log2M > kMaxTwoPassLog2 ? ((nb * bufl + 1) & ~1) + lay
-                                                               : std::max(nb * bufl, lay));
+        syn_max = std::max(syn_max, (((gd.log2M > kMaxTwoPassLog2 ? 0 : M) + nb * bufl + 1) & ~1) + lay);
         smem_p = std::max(smem_p, M + 2 * gd.fp_len + nb * bufl);
-        pl->group_cost.push_back(nb * M * (gd.log2M + 4));
+        // estimated cycles per slice of one persistent CTA (a fixed part for
+        // staging and barriers, the team transforms of the busiest warp
+        // count times active warps, and the bin write-out); fitted to
+        // per-CTA clock measurements of both kernels on GB300
+        {
+          const int thr = nb * (M >= kPerThread ? M / kPerThread : 1);
+          const double fft = (double)((thr + 31) / 32) * std::min(M, kPerThread) * (gd.log2M + 4);
+          const double rows = (double)((gd.acc_hi - gd.acc_lo + kBandThreads - 1) / kBandThreads);
+          const double nl = (double)((gd.nphases & 0xFFFF) + (gd.nphases >> 16));
+          const double fp_rows = (double)((gd.fp_len + kBandThreads - 1) / kBandThreads);
+          pl->cost_a.push_back(2700.0 + 1.1 * fft + 6.5 * fp_rows * 16.0);
+          pl->cost_s.push_back(5200.0 + 1.9 * fft + 3.5 * rows * 8.0 * (nl + 1.0));
+        }
       }
       (void)smem;
       pl->groups.push_back(gd);
@@ -295,8 +306,7 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
   pl->band_smem_s = syn_max * (int)sizeof(float2);
   pl->band_smem_p = smem_p * (int)sizeof(float2);
   if (pl->band_smem_p > 220 * 1024) return SLICQ_EUNSUPPORTED;
-  // synthesis also has 16 KB of static twiddles (227 KB per CTA at most)
-  if (pl->band_smem_a > 220 * 1024 || pl->band_smem_s > 208 * 1024) return SLICQ_EUNSUPPORTED;
+  if (pl->band_smem_a > 220 * 1024 || pl->band_smem_s > 220 * 1024) return SLICQ_EUNSUPPORTED;
 
   // ---- slice FFT geometry: N = P Q, cluster of C CTAs, <= 256 threads each
   const int logN = ilog2_64(N);
@@ -470,6 +480,91 @@ __global__ void k_tukey(int64_t M, float* hw) {
 
 size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 
+// One lane each, then every further CTA (up to `ctas`) to the group whose
+// estimated time per lane, cost / lanes, is largest.
+std::vector<int> balance_lanes(const std::vector<double>& cost, int ctas) {
+  const int G = (int)cost.size();
+  std::vector<int> lanes(G, 1);
+  for (int c = G; c < ctas; ++c) {
+    int best = 0;
+    for (int g = 1; g < G; ++g)
+      if (cost[g] * lanes[best] > cost[best] * lanes[g]) best = g;
+    ++lanes[best];
+  }
+  return lanes;
+}
+
+// CTA -> (group, lane) for the given lanes per group.
+std::vector<int2> lane_map(const std::vector<int>& lanes) {
+  std::vector<int2> map;
+  for (int g = 0; g < (int)lanes.size(); ++g)
+    for (int y = 0; y < lanes[g]; ++y) map.push_back(make_int2(g, y));
+  return map;
+}
+
+cudaError_t upload_lanes(slicq_plan* pl, bool synthesis, const std::vector<int>& lanes) {
+  const std::vector<int2> map = lane_map(lanes);
+  cudaError_t e = cudaMemcpy(synthesis ? pl->d_cta_map_s : pl->d_cta_map_a, map.data(),
+                             sizeof(int2) * map.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy(synthesis ? pl->d_lanes_s : pl->d_lanes_a, lanes.data(), sizeof(int) * lanes.size(),
+                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) (synthesis ? pl->n_cta_s : pl->n_cta_a) = (int)map.size();
+  return e;
+}
+
+// Lanes per group from measured costs: both persistent band kernels run once
+// on zeros (the timing does not depend on the values) with the same number
+// of lanes per group and four slices per lane; each group's cost is its
+// CTAs' SM clocks per slice.  The plan keeps its estimated lanes if any step
+// fails.
+void calibrate_lanes(slicq_plan* pl) {
+  const int G = pl->G;
+  const int per = std::max(1, pl->num_sms / G);
+  const std::vector<int> equal(G, per);
+  const int64_t S = 4 * (int64_t)per;
+  Workspace ws;
+  const size_t wbytes = workspace_layout_rows(pl, S, nullptr, &ws);
+  const size_t cbytes = sizeof(float2) * (size_t)(S * pl->coefs_per_slice);
+  const int ncta = per * G;
+  void* work = nullptr;
+  float2* coef = nullptr;
+  long long* d_cyc = nullptr;
+  std::vector<int> lanes[2];
+  bool ok = cudaMalloc(&work, wbytes) == cudaSuccess && cudaMalloc(&coef, cbytes) == cudaSuccess &&
+            cudaMalloc(&d_cyc, sizeof(long long) * 2 * ncta) == cudaSuccess;
+  ok = ok && cudaMemset(work, 0, wbytes) == cudaSuccess && cudaMemset(coef, 0, cbytes) == cudaSuccess;
+  ok = ok && upload_lanes(pl, false, equal) == cudaSuccess && upload_lanes(pl, true, equal) == cudaSuccess;
+  if (ok) {
+    workspace_layout_rows(pl, S, work, &ws);
+    ok = launch_band_analysis(pl, ws, 1, coef, 0, d_cyc) == cudaSuccess &&
+         launch_band_synthesis(pl, coef, 1, kSynthInverse, ws, 0, d_cyc + ncta) == cudaSuccess &&
+         cudaDeviceSynchronize() == cudaSuccess;
+  }
+  std::vector<long long> cyc(2 * (size_t)ncta, 0);
+  ok = ok && cudaMemcpy(cyc.data(), d_cyc, sizeof(long long) * cyc.size(), cudaMemcpyDeviceToHost) == cudaSuccess;
+  if (ok) {
+    for (int kind = 0; kind < 2; ++kind) {
+      std::vector<double> cost(G, 0.0);
+      for (int g = 0; g < G; ++g) {
+        double c = 0.0, n = 0.0;
+        for (int y = 0; y < per; ++y) {
+          c += (double)cyc[(size_t)kind * ncta + (size_t)g * per + y];
+          n += (double)((S - y + per - 1) / per);
+        }
+        cost[g] = std::max(1.0, c / std::max(1.0, n));
+      }
+      (kind ? pl->cost_s : pl->cost_a) = cost;
+    }
+  }
+  cudaFree(work);
+  cudaFree(coef);
+  cudaFree(d_cyc);
+  // measured costs when the runs succeeded, the estimates otherwise
+  upload_lanes(pl, false, balance_lanes(pl->cost_a, pl->num_sms));
+  upload_lanes(pl, true, balance_lanes(pl->cost_s, pl->num_sms));
+}
+
 }  // namespace
 
 slicq_status build_tables(slicq_plan* pl) {
@@ -488,24 +583,26 @@ slicq_status build_tables(slicq_plan* pl) {
   const size_t o_ga = take(sizeof(float) * (pl->win_total + 32));  // + padding
   const size_t o_gs = take(sizeof(float) * (pl->win_total + 32));  // + padding
   const size_t o_gadj = take(sizeof(float) * (pl->win_total + 32));  // + padding
-  // persistent band analysis: the same number of lanes (CTAs) per group, one
-  // CTA per SM in total (at least one per group).  A slice of any group costs
-  // a similar fixed part (staging, barriers) plus its transforms; equal lanes
-  // measured faster than lanes proportional to the transform work.
-  std::vector<int> lanes(pl->G, 1);
+  // persistent band kernels: one CTA per SM in total (at least one per
+  // group), lanes (CTAs) per group chosen so that the estimated time of a
+  // lane, cost / lanes, is as even as possible
   {
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl->device) == cudaSuccess && sms > 0)
       pl->num_sms = sms;
-    const int per = std::max(1, pl->num_sms / pl->G);
-    for (int g = 0; g < pl->G; ++g) lanes[g] = per;
-    pl->n_cta_a = per * pl->G;
   }
-  std::vector<int2> cta_map;
-  for (int g = 0; g < pl->G; ++g)
-    for (int y = 0; y < lanes[g]; ++y) cta_map.push_back(make_int2(g, y));
-  const size_t o_map = take(sizeof(int2) * cta_map.size());
-  const size_t o_lanes = take(sizeof(int) * pl->G);
+  // (these estimates from the group sizes are replaced by measured costs in
+  // calibrate_lanes once the tables exist)
+  std::vector<int> lanes_a = balance_lanes(pl->cost_a, pl->num_sms);
+  std::vector<int> lanes_s = balance_lanes(pl->cost_s, pl->num_sms);
+  std::vector<int2> map_a = lane_map(lanes_a), map_s = lane_map(lanes_s);
+  pl->n_cta_a = (int)map_a.size();
+  pl->n_cta_s = (int)map_s.size();
+  const size_t map_cap = (size_t)std::max(pl->G, pl->num_sms);  // sum of lanes at most
+  const size_t o_map_a = take(sizeof(int2) * map_cap);
+  const size_t o_lanes_a = take(sizeof(int) * pl->G);
+  const size_t o_map_s = take(sizeof(int2) * map_cap);
+  const size_t o_lanes_s = take(sizeof(int) * pl->G);
   const size_t o_hw = take(sizeof(float) * (Mtr + 1));
   const size_t o_h0 = take(sizeof(float) * L2);
   const size_t o_twlo = take(sizeof(float2) * (size_t(1) << pl->tw_lb));
@@ -526,8 +623,10 @@ slicq_status build_tables(slicq_plan* pl) {
   pl->d_gadj = (float*)(base + o_gadj);
   pl->d_hw = (float*)(base + o_hw);
   pl->d_h0 = (float*)(base + o_h0);
-  pl->d_cta_map = (int2*)(base + o_map);
-  pl->d_lanes = (int*)(base + o_lanes);
+  pl->d_cta_map_a = (int2*)(base + o_map_a);
+  pl->d_lanes_a = (int*)(base + o_lanes_a);
+  pl->d_cta_map_s = (int2*)(base + o_map_s);
+  pl->d_lanes_s = (int*)(base + o_lanes_s);
   pl->d_tw_lo = (float2*)(base + o_twlo);
   pl->d_tw_hi = (float2*)(base + o_twhi);
   pl->d_twband = (float2*)(base + o_twband);
@@ -557,9 +656,8 @@ slicq_status build_tables(slicq_plan* pl) {
     e = cudaMemcpy(pl->d_ovl_bin, pl->ovl_bin.data(), sizeof(int32_t) * pl->ovl_bin.size(),
                    cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
-    e = cudaMemcpy(pl->d_cta_map, cta_map.data(), sizeof(int2) * cta_map.size(), cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy(pl->d_lanes, lanes.data(), sizeof(int) * pl->G, cudaMemcpyHostToDevice);
+    e = upload_lanes(pl, false, lanes_a);
+  if (e == cudaSuccess) e = upload_lanes(pl, true, lanes_s);
   if (e != cudaSuccess) return SLICQ_ECUDA;
 
   // temporaries for the FP64 computation
@@ -624,6 +722,7 @@ slicq_status build_tables(slicq_plan* pl) {
   cudaFree(d_g64);
   cudaFree(d_d);
   cudaFree(d_bad);
+  if (st == SLICQ_OK) calibrate_lanes(pl);
   return st;
 }
 
