@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(kBandThreads, 1) band_analysis_persistent_kern
 // lengths)][team buffers][accumulator layers].  Per slice: pass 1, pass 2
 // (while the next slice's coefficients load into registers), weighted
 // values to the layers, then every bin of the group to the spectrum or a
-// patch row; the write-out zeroes the layers for the next slice.
+// patch row.
 
 // Zeroes n complex values at p (p 16-byte aligned) with 16-byte stores.
 __device__ __forceinline__ void zero_layers(float2* p, int n) {
@@ -252,32 +252,26 @@ struct BinSink {
 };
 
 // Bins [acc_lo, acc_hi): the sum of the NL layers in layer order (NL = 0:
-// nl layers), zeroing them for the next slice.
+// nl layers).  The bins a layer's channels cover are the same in every
+// slice and are overwritten by every slice's stores; the others stay zero
+// from the initial zeroing, so the layers need no clearing between slices.
 template <int NL>
-__device__ __forceinline__ void write_bins(const GroupDesc& gd, float2* lay, int nl, int acc_n,
+__device__ __forceinline__ void write_bins(const GroupDesc& gd, const float2* lay, int nl, int acc_n,
                                            const BinSink& out) {
-  const float2 z = make_float2(0.f, 0.f);
   for (int h = gd.acc_lo + (int)threadIdx.x; h < gd.acc_hi; h += kBandThreads) {
-    float2* p = lay + (h - gd.acc_lo);
+    const float2* p = lay + (h - gd.acc_lo);
     float2 v = p[0];
-    p[0] = z;
     if (NL > 0) {
 #pragma unroll
-      for (int l = 1; l < NL; ++l) {
-        v = c_add(v, p[l * acc_n]);
-        p[l * acc_n] = z;
-      }
+      for (int l = 1; l < NL; ++l) v = c_add(v, p[l * acc_n]);
     } else {
-      for (int l = 1; l < nl; ++l) {
-        v = c_add(v, p[l * acc_n]);
-        p[l * acc_n] = z;
-      }
+      for (int l = 1; l < nl; ++l) v = c_add(v, p[l * acc_n]);
     }
     out.put(h, v);
   }
 }
 
-__device__ __forceinline__ void write_bins_n(const GroupDesc& gd, float2* lay, int nl, int acc_n,
+__device__ __forceinline__ void write_bins_n(const GroupDesc& gd, const float2* lay, int nl, int acc_n,
                                              const BinSink& out) {
   switch (nl) {
     case 1: write_bins<1>(gd, lay, nl, acc_n, out); break;
@@ -388,7 +382,7 @@ __device__ void synthesis_two_pass(const BandArgs& a, const GroupDesc& gd, int k
     __syncwarp();  // the team has read its buffer: refill it with the next slice
     if (active && s + lanes < total) fetch(q, s + lanes);
     cp_async_commit();
-    __syncthreads();  // the previous slice's write-out has zeroed the layers
+    __syncthreads();  // the previous slice's write-out has read the layers
     if (active) {
       float2* dl = sm + q.dl;
       float2* ml = sm + q.ml;

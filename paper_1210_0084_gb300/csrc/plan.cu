@@ -513,16 +513,17 @@ cudaError_t upload_lanes(slicq_plan* pl, bool synthesis, const std::vector<int>&
   return e;
 }
 
-// Lanes per group from measured costs: both persistent band kernels run once
-// on zeros (the timing does not depend on the values) with the same number
-// of lanes per group and four slices per lane; each group's cost is its
-// CTAs' SM clocks per slice.  The plan keeps its estimated lanes if any step
-// fails.
+// Lanes per group from measured costs: both persistent band kernels run on
+// zeros (the timing does not depend on the values) with the same number of
+// lanes per group, first once to warm caches and clocks (one slice per
+// lane), then with six slices per lane; a group's cost is its CTAs' SM
+// clocks per slice in the second run.  The plan keeps its estimated lanes if
+// any step fails.
 void calibrate_lanes(slicq_plan* pl) {
   const int G = pl->G;
   const int per = std::max(1, pl->num_sms / G);
   const std::vector<int> equal(G, per);
-  const int64_t S = 4 * (int64_t)per;
+  const int64_t S = 6 * (int64_t)per;
   Workspace ws;
   const size_t wbytes = workspace_layout_rows(pl, S, nullptr, &ws);
   const size_t cbytes = sizeof(float2) * (size_t)(S * pl->coefs_per_slice);
@@ -530,29 +531,26 @@ void calibrate_lanes(slicq_plan* pl) {
   void* work = nullptr;
   float2* coef = nullptr;
   long long* d_cyc = nullptr;
-  std::vector<int> lanes[2];
   bool ok = cudaMalloc(&work, wbytes) == cudaSuccess && cudaMalloc(&coef, cbytes) == cudaSuccess &&
             cudaMalloc(&d_cyc, sizeof(long long) * 2 * ncta) == cudaSuccess;
   ok = ok && cudaMemset(work, 0, wbytes) == cudaSuccess && cudaMemset(coef, 0, cbytes) == cudaSuccess;
   ok = ok && upload_lanes(pl, false, equal) == cudaSuccess && upload_lanes(pl, true, equal) == cudaSuccess;
-  if (ok) {
-    workspace_layout_rows(pl, S, work, &ws);
+  for (int run = 0; ok && run < 2; ++run) {
+    const int64_t rows = run == 0 ? per : S;
+    workspace_layout_rows(pl, rows, work, &ws);
     ok = launch_band_analysis(pl, ws, 1, coef, 0, d_cyc) == cudaSuccess &&
-         launch_band_synthesis(pl, coef, 1, kSynthInverse, ws, 0, d_cyc + ncta) == cudaSuccess &&
-         cudaDeviceSynchronize() == cudaSuccess;
+         launch_band_synthesis(pl, coef, 1, kSynthInverse, ws, 0, d_cyc + ncta) == cudaSuccess;
   }
+  ok = ok && cudaDeviceSynchronize() == cudaSuccess;
   std::vector<long long> cyc(2 * (size_t)ncta, 0);
   ok = ok && cudaMemcpy(cyc.data(), d_cyc, sizeof(long long) * cyc.size(), cudaMemcpyDeviceToHost) == cudaSuccess;
   if (ok) {
-    for (int kind = 0; kind < 2; ++kind) {
+    for (int kind = 0; kind < 2; ++kind) {  // 0 analysis, 1 synthesis
       std::vector<double> cost(G, 0.0);
       for (int g = 0; g < G; ++g) {
-        double c = 0.0, n = 0.0;
-        for (int y = 0; y < per; ++y) {
-          c += (double)cyc[(size_t)kind * ncta + (size_t)g * per + y];
-          n += (double)((S - y + per - 1) / per);
-        }
-        cost[g] = std::max(1.0, c / std::max(1.0, n));
+        double c = 0.0;
+        for (int y = 0; y < per; ++y) c += (double)cyc[(size_t)kind * ncta + (size_t)g * per + y];
+        cost[g] = std::max(1.0, c / (double)(S));  // each lane ran S / per slices
       }
       (kind ? pl->cost_s : pl->cost_a) = cost;
     }
