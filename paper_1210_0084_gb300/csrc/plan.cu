@@ -330,7 +330,8 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
     pl->tw_lb = (ilog2_64(L2) + 1) / 2;
     pl->slice_tw_off = std::max(std::max(cs1, xs1), std::max(cs3, zs3));
     const int ntw = (1 << pl->tw_lb) + (int)(L2 >> pl->tw_lb);
-    pl->slice_smem = (pl->slice_tw_off + ntw) * (int)sizeof(float2);
+    // + the pass-2 tables of lengths P and Q
+    pl->slice_smem = (pl->slice_tw_off + ntw + P + Qn) * (int)sizeof(float2);
   }
   return SLICQ_OK;
 }

@@ -41,6 +41,7 @@ struct SliceArgs {
   const float* __restrict__ hw;   // Tukey transition, Mtr + 1 values
   const float2* __restrict__ h0;  // h_0 over the slice as pairs (h_0[2e], h_0[2e+1])
   TwiddleTables tw;               // global two-level tables (copied to shared memory)
+  const float2* __restrict__ twband;  // pass-2 tables of lengths 16..1024, [r][j] per length
   const float2* __restrict__ tw4; // four-step twiddles exp(-2 pi i q u / N) at [u Q + q]
   int tw_off;                     // shared-memory offset (float2) of the table copy
   float* ola_patch;               // [slice][2][Mtr]
@@ -91,37 +92,50 @@ struct Geo {
 // returns input element e (0 <= e < N).  On return res[i * R2q + r] holds
 // Z[u + P v] for u = rank * P/C + ul, v = (tt + TTq i) + r R1q, and the shared
 // memory may be reused after a __syncthreads().
-template <int SIGN>
-struct SliceTw {  // exp(SIGN 2 pi i j r / 2^(log2N2 - shift)) from the shared tables
-  SmemTwiddles t;
-  int shift;
+// Pass-2 twiddle exp(SIGN 2 pi i j r / 2^LOGL) of a team transform of length
+// 2^LOGL (a column or row DFT) from its shared [r][j] table: one load.
+template <int LOGL, int SIGN>
+struct PassTw {
+  const float2* t;
   __device__ __forceinline__ float2 operator()(int j, int r) const {
-    const float2 w = t((uint32_t)(j * r) << shift);
+    const float2 w = t[r * Team<LOGL>::R1 + j];
     return SIGN < 0 ? w : c_conj(w);
   }
 };
 
-// Copy the two-level twiddle tables to shared memory (caller synchronises).
-__device__ __forceinline__ SmemTwiddles stage_twiddles(const SliceArgs& a, float2* sm) {
+// Shared-memory copies: the two-level table exp(-2 pi i t / 2N) at tw_off,
+// then the pass-2 tables of lengths P and Q (caller synchronises).
+struct SliceTables {
+  SmemTwiddles tw;
+  const float2* twP;
+  const float2* twQ;
+};
+
+template <int LOGP, int LOGQ>
+__device__ __forceinline__ SliceTables stage_twiddles(const SliceArgs& a, float2* sm) {
+  constexpr int P = 1 << LOGP, Q = 1 << LOGQ;
   float2* lo = sm + a.tw_off;
   const int nlo = 1 << a.tw.lb;
   float2* hi = lo + nlo;
   const int nhi = (2 * a.N) >> a.tw.lb;
+  float2* tp = hi + nhi;
+  float2* tq = tp + P;
   for (int i = threadIdx.x; i < nlo; i += blockDim.x) lo[i] = __ldg(a.tw.lo + i);
   for (int i = threadIdx.x; i < nhi; i += blockDim.x) hi[i] = __ldg(a.tw.hi + i);
-  return SmemTwiddles{lo, hi, a.tw.lb};
+  for (int i = threadIdx.x; i < P; i += blockDim.x) tp[i] = __ldg(a.twband + (P - 16) + i);
+  for (int i = threadIdx.x; i < Q; i += blockDim.x) tq[i] = __ldg(a.twband + (Q - 16) + i);
+  return SliceTables{SmemTwiddles{lo, hi, a.tw.lb}, tp, tq};
 }
 
 template <int LOGP, int LOGQ, int SIGN, class Load>
 __device__ __forceinline__ void fourstep(const SliceArgs& a, cg::cluster_group& cluster,
-                                         float2* sm, const SmemTwiddles& tws, Load load,
+                                         float2* sm, const SliceTables& tabs, Load load,
                                          float2* res, int& ul_out, int& tt_out) {
   using G = Geo<LOGP, LOGQ>;
   using TP = typename G::TP;
   using TQ = typename G::TQ;
   const int t = threadIdx.x;
   const int rank = (int)cluster.block_rank();
-  const int log2N2 = LOGP + LOGQ + 1;
 
   // ---- phase 1: column DFTs over p for the CTA's columns q
   {
@@ -133,7 +147,7 @@ __device__ __forceinline__ void fourstep(const SliceArgs& a, cg::cluster_group& 
     team_pass1<LOGP, SIGN>(tt, buf, [&](int p) { return load(p * G::Q + q); });
     __syncthreads();
     float2 col[TP::HELD];
-    team_pass2<LOGP, SIGN>(tt, buf, SliceTw<SIGN>{tws, log2N2 - LOGP}, col);
+    team_pass2<LOGP, SIGN>(tt, buf, PassTw<LOGP, SIGN>{tabs.twP}, col);
     __syncthreads();
     // four-step twiddle W_N^{q u} = W_2N^{2 q u}, then the exchange layout [ql][u]
 #pragma unroll
@@ -180,7 +194,7 @@ __device__ __forceinline__ void fourstep(const SliceArgs& a, cg::cluster_group& 
       for (int r = 0; r < TQ::R1; ++r) buf[TQ::pad1(j, r)] = v[r];
     }
     __syncthreads();
-    team_pass2<LOGQ, SIGN>(tt, buf, SliceTw<SIGN>{tws, log2N2 - LOGQ}, res);
+    team_pass2<LOGQ, SIGN>(tt, buf, PassTw<LOGQ, SIGN>{tabs.twQ}, res);
   }
   ul_out = ul;
   tt_out = tt;
@@ -189,7 +203,7 @@ __device__ __forceinline__ void fourstep(const SliceArgs& a, cg::cluster_group& 
 // ------------------------------------------------------------- forward ---
 
 template <int LOGP, int LOGQ>
-__global__ void __launch_bounds__(kSliceMaxThreads) slice_forward_kernel(SliceArgs a) {
+__global__ void __launch_bounds__(kSliceMaxThreads, 2) slice_forward_kernel(SliceArgs a) {
   using G = Geo<LOGP, LOGQ>;
   using TQ = typename G::TQ;
   extern __shared__ float2 sm[];
@@ -226,13 +240,14 @@ __global__ void __launch_bounds__(kSliceMaxThreads) slice_forward_kernel(SliceAr
 
   // the band analysis that follows in the same stream counts its work items from 0
   if (blockIdx.x == 0 && threadIdx.x == 0) *a.items = 0ull;
-  const SmemTwiddles tws = stage_twiddles(a, sm);
+  const SliceTables tabs = stage_twiddles<LOGP, LOGQ>(a, sm);
+  const SmemTwiddles& tws = tabs.tw;
   __syncthreads();
   const int Pc = 1 << a.logPc;
   {
     float2 res[TQ::HELD];
     int ul, tt;
-    fourstep<LOGP, LOGQ, -1>(a, cluster, sm, tws, load, res, ul, tt);
+    fourstep<LOGP, LOGQ, -1>(a, cluster, sm, tabs, load, res, ul, tt);
     __syncthreads();
     // Z to shared memory, column-major [v][ul], for the even/odd split (needs
     // Z[N - k] from the partner row): local reads, partner reads and the
@@ -306,7 +321,7 @@ __device__ __forceinline__ void ola_combine(const SliceArgs& a, int64_t tr_slot,
 }
 
 template <int LOGP, int LOGQ>
-__global__ void __launch_bounds__(kSliceMaxThreads) slice_inverse_kernel(SliceArgs a) {
+__global__ void __launch_bounds__(kSliceMaxThreads, 2) slice_inverse_kernel(SliceArgs a) {
   using G = Geo<LOGP, LOGQ>;
   using TQ = typename G::TQ;
   extern __shared__ float2 sm[];
@@ -324,7 +339,8 @@ __global__ void __launch_bounds__(kSliceMaxThreads) slice_inverse_kernel(SliceAr
   // the band synthesis of the next call counts its work items from 0 (it has
   // finished for this call: it precedes this kernel in the stream)
   if (blockIdx.x == 0 && threadIdx.x == 0) *a.items = 0ull;
-  const SmemTwiddles tws = stage_twiddles(a, sm);
+  const SliceTables tabs = stage_twiddles<LOGP, LOGQ>(a, sm);
+  const SmemTwiddles& tws = tabs.tw;
   __syncthreads();
   // Z[k] = (H[k] + conj H[N-k]) + i e^{+2 pi i k / 2N} (H[k] - conj H[N-k])
   auto load = [&](int k) -> float2 {
@@ -338,7 +354,7 @@ __global__ void __launch_bounds__(kSliceMaxThreads) slice_inverse_kernel(SliceAr
   {
     float2 res[TQ::HELD];
     int ul, tt;
-    fourstep<LOGP, LOGQ, +1>(a, cluster, sm, tws, load, res, ul, tt);
+    fourstep<LOGP, LOGQ, +1>(a, cluster, sm, tabs, load, res, ul, tt);
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < TQ::J2; ++i)
@@ -471,6 +487,7 @@ SliceArgs make_args(const slicq_plan* pl, const Workspace& ws, int64_t n) {
   a.h0 = reinterpret_cast<const float2*>(pl->d_h0);
   a.tw = TwiddleTables{pl->d_tw_lo, pl->d_tw_hi, pl->tw_lb};
   a.tw_off = pl->slice_tw_off;
+  a.twband = pl->d_twband;
   a.tw4 = pl->d_tw4;
   a.ola_patch = ws.ola_patch;
   a.ola_cnt = ws.ola_cnt;
