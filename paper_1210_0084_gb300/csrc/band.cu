@@ -113,6 +113,12 @@ __device__ __forceinline__ void band_three_pass(bool active, int tt, float2* buf
   }
 }
 
+// A channel whose support J_k lies strictly between DC and Nyquist: no wrap
+// around the circle, no mirrored bins, every bin its own half-spectrum bin.
+__device__ __forceinline__ bool simple_channel(const BandDesc& bd, int N) {
+  return bd.j0 > 0 && bd.j0 + bd.len - 1 < N;
+}
+
 template <int LOGM>
 __device__ void analysis_persistent(const BandArgs& a, const GroupDesc& gd, int lane, int lanes,
                                     int64_t total, float2* sm) {
@@ -124,17 +130,42 @@ __device__ void analysis_persistent(const BandArgs& a, const GroupDesc& gd, int 
   const int t = threadIdx.x;
   const int nb = gd.band_end - gd.band_begin;
   const int bl = t / TT;
-  const int tt = t - bl * TT;
   const bool active = bl < nb;
   const BandDesc bd = a.bands[gd.band_begin + (active ? bl : 0)];
   const int twoN = 2 * a.N;
   float2* s_tw = sm;
   float2* s_x0 = sm + M;
   float2* s_x1 = s_x0 + gd.fp_len;
-  float2* buf = s_x1 + gd.fp_len + bl * BUFL;
+  const int buf_off = M + 2 * gd.fp_len + bl * BUFL;
   const float* __restrict__ g = a.win + bd.win_off;
+  const bool simple = simple_channel(bd, a.N);
   if (!THREE)
     for (int i = t; i < M; i += blockDim.x) s_tw[i] = __ldg(a.twband + (M - 16) + i);
+  // window values of the pass-1 inputs, 0 outside the support: the same in
+  // every slice (registers; two-pass lengths)
+  float w[THREE ? 1 : T::J1][THREE ? 1 : T::R1];
+  if constexpr (!THREE) {
+    const int tt = t - bl * TT;
+#pragma unroll
+    for (int i = 0; i < T::J1; ++i)
+#pragma unroll
+      for (int r = 0; r < T::R1; ++r) {
+        const int o = (tt + T::TT * i + r * T::R2 - bd.j0) & (M - 1);
+        w[i][r] = o < bd.len ? __ldg(g + o) : 0.f;
+      }
+  }
+  // The loop takes these integers through an empty asm each slice so that
+  // the compiler recomputes the addresses instead of keeping all of them
+  // live across the loop.
+  struct Opaque {
+    int tt, j0, len, buf;
+  };
+  const Opaque op0{t - bl * TT, bd.j0, bd.len, buf_off};
+  auto opaque = [&]() {
+    Opaque o = op0;
+    asm volatile("" : "+r"(o.tt), "+r"(o.j0), "+r"(o.len), "+r"(o.buf));
+    return o;
+  };
   auto stage = [&](int64_t s, float2* dst) {
     const float2* src = a.spec + s * a.spec_stride + gd.fp_lo;
     for (int i = 2 * t; i < gd.fp_len; i += 2 * (int)blockDim.x) cp_async16(dst + i, src + i);
@@ -148,40 +179,60 @@ __device__ void analysis_persistent(const BandArgs& a, const GroupDesc& gd, int 
     cp_async_commit();
     cp_async_wait<1>();
     __syncthreads();  // this slice's block (and, first time, the twiddles) are in
-    // every load is issued; out-of-support residues get weight 0 (the
-    // window table has padding after its last channel)
-    auto load = [&](int idx) -> float2 {
-      const int o = (idx - bd.j0) & (M - 1);
-      const bool in = o < bd.len;
-      const int oc = in ? o : 0;
-      int b = bd.j0 + oc;
+    const Opaque q = opaque();
+    float2* buf = sm + q.buf;
+    float2* out = a.coef + s * a.cps + bd.coef_off;
+    // general input element idx: the bin of the residue (circular, mirrored
+    // bins conjugated), weight 0 outside the support
+    auto load_general = [&](int idx, float wv) -> float2 {
+      const int o = (idx - q.j0) & (M - 1);
+      const int oc = o < q.len ? o : 0;
+      int b = q.j0 + oc;
       if (b >= twoN) b -= twoN;
       const bool mir = b > a.N;
       float2 x = X[mir ? twoN - b : b];
-      const float w = __ldg(g + oc);
       if (mir) x.y = -x.y;
-      return c_scale(x, in ? w : 0.f);
+      return c_scale(x, wv);
     };
     if constexpr (THREE) {
-      float2* out = a.coef + s * a.cps + bd.coef_off;
-      band_three_pass<LOGM, +1>(active, tt, buf, a.tw4096, load,
+      band_three_pass<LOGM, +1>(active, q.tt, buf, a.tw4096,
+                                [&](int idx) {
+                                  const int o = (idx - q.j0) & (M - 1);
+                                  return load_general(idx, o < q.len ? __ldg(g + o) : 0.f);
+                                },
                                 [&](int i, float2 v) { __stcs(out + i, v); });
       __syncthreads();
       continue;
-    }
-    if (active) team_pass1<THREE ? 4 : LOGM, +1>(tt, buf, load);
-    __syncwarp();  // a team lies inside one warp
-    if (active) {
-      float2 res[T::HELD];
-      constexpr int LP = THREE ? 10 : LOGM;
-      team_pass2<LP, +1>(tt, buf, [&](int j, int r) { return c_conj(s_tw[r * T::R1 + j]); }, res);
-      float2* out = a.coef + s * a.cps + bd.coef_off;
+    } else {
+      float2 v[T::J1][T::R1];
+      if (active) {
+        if (simple) {
 #pragma unroll
-      for (int i = 0; i < T::J2; ++i)
+          for (int i = 0; i < T::J1; ++i)
 #pragma unroll
-        for (int r = 0; r < T::R2; ++r) __stcs(out + team_out_index<LP>(tt, i, r), res[i * T::R2 + r]);
+            for (int r = 0; r < T::R1; ++r) {
+              const int o = (q.tt + T::TT * i + r * T::R2 - q.j0) & (M - 1);
+              v[i][r] = c_scale(X[q.j0 + (o < q.len ? o : 0)], w[i][r]);
+            }
+        } else {
+#pragma unroll
+          for (int i = 0; i < T::J1; ++i)
+#pragma unroll
+            for (int r = 0; r < T::R1; ++r) v[i][r] = load_general(q.tt + T::TT * i + r * T::R2, w[i][r]);
+        }
+        team_pass1_regs<LOGM, +1>(q.tt, buf, v);
+      }
+      __syncwarp();  // a team lies inside one warp
+      if (active) {
+        float2 res[T::HELD];
+        team_pass2<LOGM, +1>(q.tt, buf, [&](int j, int r) { return c_conj(s_tw[r * T::R1 + j]); }, res);
+#pragma unroll
+        for (int i = 0; i < T::J2; ++i)
+#pragma unroll
+          for (int r = 0; r < T::R2; ++r) __stcs(out + team_out_index<LOGM>(q.tt, i, r), res[i * T::R2 + r]);
+      }
+      __syncthreads();  // the footprint buffer is refilled two slices later
     }
-    __syncthreads();  // the footprint buffer is refilled two slices later
   }
   cp_async_wait<0>();
 }
@@ -316,6 +367,7 @@ __device__ void synthesis_two_pass(const BandArgs& a, const GroupDesc& gd, int k
   const int nl = (gd.nphases & 0xFFFF) + (gd.nphases >> 16);
   const int lay_off = (M + nb * T::BUF + 1) & ~1;
   float2* lay = sm + lay_off;
+  const bool simple = simple_channel(bd, a.N);
 
   for (int i = t; i < M; i += kBandThreads) sm[i] = __ldg(a.twband + (M - 16) + i);
   zero_layers(lay, nl * acc_n);
@@ -386,19 +438,29 @@ __device__ void synthesis_two_pass(const BandArgs& a, const GroupDesc& gd, int k
     if (active) {
       float2* dl = sm + q.dl;
       float2* ml = sm + q.ml;
+      if (simple) {
 #pragma unroll
-      for (int i = 0; i < T::J2; ++i)
+        for (int i = 0; i < T::J2; ++i)
 #pragma unroll
-        for (int r = 0; r < T::R2; ++r) {
-          const int o = (team_out_index<LOGM>(q.tt, i, r) - q.j0) & (M - 1);
-          int b = q.j0 + o;
-          if (b >= twoN) b -= twoN;
-          if (o < q.len) {
-            const float2 y = c_scale(res[i * T::R2 + r], w[i * T::R2 + r]);
-            if (b <= a.N) dl[b] = y;
-            if (b == 0 || b >= a.N) ml[b == 0 ? 0 : twoN - b] = c_conj(y);
+          for (int r = 0; r < T::R2; ++r) {
+            const int o = (team_out_index<LOGM>(q.tt, i, r) - q.j0) & (M - 1);
+            if (o < q.len) dl[q.j0 + o] = c_scale(res[i * T::R2 + r], w[i * T::R2 + r]);
           }
-        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < T::J2; ++i)
+#pragma unroll
+          for (int r = 0; r < T::R2; ++r) {
+            const int o = (team_out_index<LOGM>(q.tt, i, r) - q.j0) & (M - 1);
+            int b = q.j0 + o;
+            if (b >= twoN) b -= twoN;
+            if (o < q.len) {
+              const float2 y = c_scale(res[i * T::R2 + r], w[i * T::R2 + r]);
+              if (b <= a.N) dl[b] = y;
+              if (b == 0 || b >= a.N) ml[b == 0 ? 0 : twoN - b] = c_conj(y);
+            }
+          }
+      }
     }
     __syncthreads();
     write_bins_n(gd, lay, nl, acc_n, BinSink(a, gd, s));
