@@ -517,10 +517,11 @@ cudaError_t upload_lanes(slicq_plan* pl, bool synthesis, const std::vector<int>&
 // Lanes per group from measured costs: both persistent band kernels run on
 // zeros (the timing does not depend on the values) with the same number of
 // lanes per group, first once to warm caches and clocks (one slice per
-// lane), then with six slices per lane; a group's cost is its CTAs' SM
-// clocks per slice in the second run.  The plan keeps its estimated lanes if
-// any step fails.
+// lane), then three times with six slices per lane; a group's cost is the
+// median over the three runs of its CTAs' SM clocks per slice.  The plan
+// keeps its estimated lanes if any step fails.
 void calibrate_lanes(slicq_plan* pl) {
+  constexpr int kRuns = 3;
   const int G = pl->G;
   const int per = std::max(1, pl->num_sms / G);
   const std::vector<int> equal(G, per);
@@ -533,25 +534,31 @@ void calibrate_lanes(slicq_plan* pl) {
   float2* coef = nullptr;
   long long* d_cyc = nullptr;
   bool ok = cudaMalloc(&work, wbytes) == cudaSuccess && cudaMalloc(&coef, cbytes) == cudaSuccess &&
-            cudaMalloc(&d_cyc, sizeof(long long) * 2 * ncta) == cudaSuccess;
+            cudaMalloc(&d_cyc, sizeof(long long) * 2 * ncta * kRuns) == cudaSuccess;
   ok = ok && cudaMemset(work, 0, wbytes) == cudaSuccess && cudaMemset(coef, 0, cbytes) == cudaSuccess;
   ok = ok && upload_lanes(pl, false, equal) == cudaSuccess && upload_lanes(pl, true, equal) == cudaSuccess;
-  for (int run = 0; ok && run < 2; ++run) {
+  for (int run = 0; ok && run <= kRuns; ++run) {  // run 0 warms up (and is overwritten)
     const int64_t rows = run == 0 ? per : S;
     workspace_layout_rows(pl, rows, work, &ws);
-    ok = launch_band_analysis(pl, ws, 1, coef, 0, d_cyc) == cudaSuccess &&
-         launch_band_synthesis(pl, coef, 1, kSynthInverse, ws, 0, d_cyc + ncta) == cudaSuccess;
+    long long* c = d_cyc + (size_t)std::max(run - 1, 0) * 2 * ncta;
+    ok = launch_band_analysis(pl, ws, 1, coef, 0, c) == cudaSuccess &&
+         launch_band_synthesis(pl, coef, 1, kSynthInverse, ws, 0, c + ncta) == cudaSuccess;
   }
   ok = ok && cudaDeviceSynchronize() == cudaSuccess;
-  std::vector<long long> cyc(2 * (size_t)ncta, 0);
+  std::vector<long long> cyc(2 * (size_t)ncta * kRuns, 0);
   ok = ok && cudaMemcpy(cyc.data(), d_cyc, sizeof(long long) * cyc.size(), cudaMemcpyDeviceToHost) == cudaSuccess;
   if (ok) {
     for (int kind = 0; kind < 2; ++kind) {  // 0 analysis, 1 synthesis
       std::vector<double> cost(G, 0.0);
       for (int g = 0; g < G; ++g) {
-        double c = 0.0;
-        for (int y = 0; y < per; ++y) c += (double)cyc[(size_t)kind * ncta + (size_t)g * per + y];
-        cost[g] = std::max(1.0, c / (double)(S));  // each lane ran S / per slices
+        double c[kRuns];
+        for (int run = 0; run < kRuns; ++run) {
+          c[run] = 0.0;
+          for (int y = 0; y < per; ++y)
+            c[run] += (double)cyc[((size_t)run * 2 + kind) * ncta + (size_t)g * per + y];
+        }
+        std::sort(c, c + kRuns);
+        cost[g] = std::max(1.0, c[kRuns / 2] / (double)S);  // each lane ran S / per slices
       }
       (kind ? pl->cost_s : pl->cost_a) = cost;
     }
