@@ -38,7 +38,8 @@ WORKLOAD = dict(fs=44100.0, fmin=32.7, fmax=22050.0, bins_per_octave=48, slice_l
                 trans_len=16384, seconds=60, channels=2)
 WORKLOAD_NAME = ("60 s stereo 44.1 kHz, pink noise + 20 decaying harmonic tones; Hann CQ windows "
                  "B=48, fmin=32.7 Hz, fmax=22050 Hz; slice 2N=65536, transition 16384")
-KERNELS = ("slice_forward", "band_analysis", "band_synthesis", "band_boundary", "slice_inverse")
+KERNELS = ("slice_forward", "band_analysis", "band_synthesis", "band_boundary", "slice_inverse",
+           "slice_ola")
 
 
 def _env_int(name, default):
@@ -360,11 +361,12 @@ def main():
     for name, t in traced:
         per[name].append(t)
     cps = plan.coefs_per_slice
-    # band_boundary moves no algorithmic bytes (it adds the partial sums of
-    # the bins two band groups share)
+    # band_boundary and slice_ola move no algorithmic bytes (they add the two
+    # partial sums of the bins two band groups share and of the transition
+    # samples two slices share)
     alg_bytes = {"slice_forward": batch * n * 4, "band_analysis": batch * S * cps * 8,
                  "band_synthesis": batch * S * cps * 8, "band_boundary": 0,
-                 "slice_inverse": batch * n * 4}
+                 "slice_inverse": batch * n * 4, "slice_ola": 0}
     peak, peak_kind = _peaks()
     kern = {}
     for k in KERNELS:

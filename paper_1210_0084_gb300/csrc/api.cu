@@ -76,8 +76,7 @@ size_t workspace_layout(const slicq_plan* pl, int64_t n, int64_t batch, void* ba
   const size_t o_items = take(2 * sizeof(unsigned long long));
   const size_t o_spec = take(sizeof(float2) * slices * w.spec_stride);
   const size_t o_bp = take(sizeof(float2) * slices * 2 * std::max(pl->ovl_total, 1));
-  const size_t o_op = take(sizeof(float) * slices * 2 * pl->params.trans_len);
-  const size_t o_oc = take(sizeof(uint32_t) * slices * pl->C);
+  const size_t o_op = take(sizeof(float) * slices * 2 * ((pl->params.trans_len + 3) & ~int64_t(3)));
   w.bytes = off;
   if (base) {
     char* b = (char*)base;
@@ -85,7 +84,6 @@ size_t workspace_layout(const slicq_plan* pl, int64_t n, int64_t batch, void* ba
     w.spec = (float2*)(b + o_spec);
     w.band_patch = (float2*)(b + o_bp);
     w.ola_patch = (float*)(b + o_op);
-    w.ola_cnt = (uint32_t*)(b + o_oc);
   }
   if (ws) *ws = w;
   return off;
@@ -101,8 +99,7 @@ size_t workspace_layout_rows(const slicq_plan* pl, int64_t rows, void* base, Wor
   const size_t o_items = take(2 * sizeof(unsigned long long));
   const size_t o_spec = take(sizeof(float2) * rows * w.spec_stride);
   const size_t o_bp = take(sizeof(float2) * rows * 2 * std::max(pl->ovl_total, 1));
-  const size_t o_op = take(sizeof(float) * rows * 2 * pl->params.trans_len);
-  const size_t o_oc = take(sizeof(uint32_t) * rows * pl->C);
+  const size_t o_op = take(sizeof(float) * rows * 2 * ((pl->params.trans_len + 3) & ~int64_t(3)));
   w.bytes = off;
   if (base) {
     char* b = (char*)base;
@@ -110,7 +107,6 @@ size_t workspace_layout_rows(const slicq_plan* pl, int64_t rows, void* base, Wor
     w.spec = (float2*)(b + o_spec);
     w.band_patch = (float2*)(b + o_bp);
     w.ola_patch = (float*)(b + o_op);
-    w.ola_cnt = (uint32_t*)(b + o_oc);
   }
   if (ws) *ws = w;
   return off;
@@ -250,6 +246,8 @@ static slicq_status synthesis(const slicq_plan* plan, const float* d_coef, int64
     if (e == cudaSuccess)
       e = traced(plan, 3, stream, [&] {
         return launch_slice_inverse(plan, n_samples, batch, kind, ws, d_out, stream); });
+    if (e == cudaSuccess)
+      e = traced(plan, 5, stream, [&] { return launch_slice_ola(plan, n_samples, batch, ws, d_out, stream); });
     return from_cuda(e);
   });
 }

@@ -207,6 +207,7 @@ slicq_status slicq_batch_inverse(const slicq_batch* b, const float* d_coef, floa
     cudaError_t e = launch_band_synthesis(sb.pl, coef, 1, kSynthInverse, ws, sb.st);
     if (e == cudaSuccess) e = launch_band_boundaries(sb.pl, 1, ws, sb.st);
     if (e == cudaSuccess) e = launch_slice_inverse(sb.pl, 0, 1, kSynthInverse, ws, d_sig_out, sb.st, sb.d_rows);
+    if (e == cudaSuccess) e = launch_slice_ola(sb.pl, 0, 1, ws, d_sig_out, sb.st, sb.d_rows);
     return e;
   });
 }

@@ -155,8 +155,7 @@ struct Workspace {
   int64_t spec_stride = 0;         // complex values per slice spectrum row
   float2* spec = nullptr;          // [batch * S][spec_stride]
   float2* band_patch = nullptr;    // [batch * S][G - 1][2][max_ovl]
-  float* ola_patch = nullptr;      // [batch * S][2][M]
-  uint32_t* ola_cnt = nullptr;     // [batch * S][C]
+  float* ola_patch = nullptr;      // [batch * S][2][M rounded up to 4]: the two sides of each transition
   size_t bytes = 0;
 };
 size_t workspace_layout(const slicq_plan* pl, int64_t n_samples, int64_t batch,
@@ -183,5 +182,10 @@ cudaError_t launch_slice_inverse(const slicq_plan* pl, int64_t n,
                                  int64_t batch, SynthKind kind,
                                  const Workspace& ws, float* out,
                                  cudaStream_t st, const RowDesc* rows = nullptr);
+// Adds the two sides of every transition into the output (after
+// launch_slice_inverse).
+cudaError_t launch_slice_ola(const slicq_plan* pl, int64_t n, int64_t batch,
+                             const Workspace& ws, float* out, cudaStream_t st,
+                             const RowDesc* rows = nullptr);
 
 }  // namespace slicq

@@ -11,9 +11,9 @@
 // with an N-point complex DFT, multiplied by the dual slicing window
 // (indicator of the support of h_0; h_0 itself for the adjoint) and
 // overlap-added.  Samples where only this slice contributes are stored
-// directly; in each transition both slices hand their values over and the
-// second to arrive stores the sum (a + b == b + a), so the result is
-// deterministic and needs no zero-filled output.
+// directly; the samples of each transition go to two patch rows (side 0:
+// the earlier slice, side 1: the later one) that slice_ola_kernel adds, so
+// the result is deterministic and needs no zero-filled output.
 //
 // The N-point DFT is a four-step transform N = P Q distributed over the C
 // CTAs of the cluster: column DFTs (length P) over the CTA's Q/C columns,
@@ -44,8 +44,8 @@ struct SliceArgs {
   const float2* __restrict__ twband;  // pass-2 tables of lengths 16..1024, [r][j] per length
   const float2* __restrict__ tw4; // four-step twiddles exp(-2 pi i q u / N) at [u Q + q]
   int tw_off;                     // shared-memory offset (float2) of the table copy
-  float* ola_patch;               // [slice][2][Mtr]
-  uint32_t* ola_cnt;              // [slice][C]
+  float* ola_patch;               // [slice][2][ola_stride]: the two sides of each transition
+  int ola_stride;                 // Mtr rounded up to a multiple of 4
   unsigned long long* items;      // band-kernel work counter this launch resets
   const RowDesc* __restrict__ rows;  // ragged batch: per-row clip description (or null)
   int adjoint;                    // multiply the output by h_0 instead of 1
@@ -293,39 +293,11 @@ __global__ void __launch_bounds__(kSliceMaxThreads, 2) slice_forward_kernel(Slic
 
 // ------------------------------------------------------------- inverse ---
 
-// Hand one transition over or, as the second arriver, store the sum.
-// EACH(fn) calls fn(o, tpos, value) for every sample of the transition that
-// this CTA holds.
-template <class Each>
-__device__ __forceinline__ void ola_combine(const SliceArgs& a, int64_t tr_slot, int side,
-                                            int rank, int* s_flag, float* out, int n32, Each each) {
-  float* mine = a.ola_patch + (tr_slot * 2 + side) * (int64_t)a.Mtr;
-  const float* other = a.ola_patch + (tr_slot * 2 + (1 - side)) * (int64_t)a.Mtr;
-  each([&](int o, int tpos, float v) { mine[o] = v; });
-  // barrier, then one thread fences and moves the counter (the pattern of a
-  // grid-wide barrier): the CTA's slot writes are ordered before it
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const unsigned old = atomicInc(a.ola_cnt + tr_slot * a.C + rank, 1u);
-    __threadfence();
-    *s_flag = (old == 1u);
-  }
-  __syncthreads();
-  if (*s_flag) {
-    each([&](int o, int tpos, float v) {
-      if (tpos < n32) out[tpos] = v + __ldcg(other + o);
-    });
-  }
-  __syncthreads();
-}
-
 template <int LOGP, int LOGQ>
 __global__ void __launch_bounds__(kSliceMaxThreads, 2) slice_inverse_kernel(SliceArgs a) {
   using G = Geo<LOGP, LOGQ>;
   using TQ = typename G::TQ;
   extern __shared__ float2 sm[];
-  __shared__ int s_flag;
   cg::cluster_group cluster = cg::this_cluster();
   const int64_t s = blockIdx.x / a.C;
   int64_t sig_off;
@@ -363,74 +335,83 @@ __global__ void __launch_bounds__(kSliceMaxThreads, 2) slice_inverse_kernel(Slic
   }
   __syncthreads();
 
-  // Time samples 2n, 2n+1 of z[n], n = u + P v; this CTA holds u in
-  // [rank Pc, (rank+1) Pc).  Each region of the slice (where only this slice
-  // contributes; the right and left transitions) is visited over its own
-  // index range.
+  // Time samples j = 2n, 2n+1 of z[n], n = u + P v; this CTA holds u in
+  // [rank Pc, (rank+1) Pc), a thread one u and every v it visits.  With
+  // d = j - N: |d| <= a0 only this slice contributes (stored directly);
+  // a0 < d < a0 + M is the right transition (shared with slice m+1, this
+  // slice is side 0, offset d - a0) and -(a0 + M) < d < -a0 the left one
+  // (shared with slice m-1, side 1, offset j - a0).
   const int Pc = 1 << a.logPc;
   const int rank = (int)cluster.block_rank();
-  const int a0 = (N - a.Mtr) >> 1;
+  const int Mtr = a.Mtr;
+  const int a0 = (N - Mtr) >> 1;
   const int base = (m - 1) * N;
   float* out = a.out + sig_off;
-  auto tpos_of = [&](int j) -> int {
-    int t = base + j;
-    if (t < 0) t += L32; else if (t >= L32) t -= L32;
-    return t;
-  };
-  auto weighted = [&](int j, float x) -> float { return a.adjoint ? x * slicing_window(a, j) : x; };
-  // fn(n, z) for the held elements with n0 <= n < n1
-  auto for_range = [&](int n0, int n1, auto&& fn) {
-    if (n0 >= n1) return;
-    const int v0 = n0 >> LOGP, v1 = (n1 - 1) >> LOGP;
-    const int cnt = (v1 - v0 + 1) << a.logPc;
-    for (int idx = threadIdx.x; idx < cnt; idx += blockDim.x) {
-      const int ul = idx & (Pc - 1);
-      const int v = v0 + (idx >> a.logPc);
-      const int n = rank * Pc + ul + (v << LOGP);
-      if (n >= n0 && n < n1) fn(n, sm[ul * G::ZS3 + v]);
+  float* pr = a.ola_patch + ((tr0 + m) * 2 + 0) * (int64_t)a.ola_stride;
+  float* pl = a.ola_patch + ((tr0 + (m + Sc - 1) % Sc) * 2 + 1) * (int64_t)a.ola_stride;
+  const bool vec = (sig_off & 1) == 0 && (a0 & 1) == 0;  // 8-byte pair stores
+  // one sample: direct, a transition side, or outside the support
+  auto put = [&](int j, float x) {
+    const int d = j - N;
+    if (d >= -a0 && d <= a0) {
+      int t = base + j;
+      if (t < 0) t += L32; else if (t >= L32) t -= L32;
+      if (t < n32) out[t] = x;
+    } else if (d > a0 && d < a0 + Mtr) {
+      pr[d - a0] = a.adjoint ? x * slicing_window(a, j) : x;
+    } else if (d < -a0 && d > -a0 - Mtr) {
+      pl[j - a0] = a.adjoint ? x * slicing_window(a, j) : x;
     }
   };
-
-  // samples with |j - N| <= a0: only this slice contributes
-  for_range((N - a0) >> 1, ((N + a0) >> 1) + 1, [&](int n, float2 z) {
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int j = 2 * n + h;
-      if (abs(j - N) <= a0) {
-        const int t = tpos_of(j);
-        if (t < n32) out[t] = weighted(j, h ? z.y : z.x);
-      }
+  // rows v whose samples can lie in the support |d| < a0 + M
+  const int n_lo = max(0, (N - a0 - Mtr) >> 1), n_hi = min(N - 1, (N + a0 + Mtr) >> 1);
+  const int v_lo = n_lo >> LOGP, v_hi = n_hi >> LOGP;
+  const int ul = threadIdx.x & (Pc - 1);
+  const int u = rank * Pc + ul;
+  for (int v = v_lo + ((int)threadIdx.x >> a.logPc); v <= v_hi; v += (int)blockDim.x >> a.logPc) {
+    const float2 z = sm[ul * G::ZS3 + v];
+    const int j = 2 * (u + (v << LOGP));
+    const int d = j - N;
+    if (vec && d >= -a0 && d + 1 <= a0) {  // both samples direct
+      int t = base + j;
+      if (t < 0) t += L32; else if (t >= L32) t -= L32;
+      if (t + 1 < n32) *reinterpret_cast<float2*>(out + t) = z;
+      else if (t < n32) out[t] = z.x;
+    } else if (vec && !a.adjoint && d > a0 && d + 1 < a0 + Mtr) {  // both in the right transition
+      *reinterpret_cast<float2*>(pr + (d - a0)) = z;
+    } else if (vec && !a.adjoint && d < -a0 - 1 && d > -a0 - Mtr) {  // both in the left transition
+      *reinterpret_cast<float2*>(pl + (j - a0)) = z;
+    } else {
+      put(j, z.x);
+      put(j + 1, z.y);
     }
-  });
-
-  // transitions, offsets o in [1, M-1]: right (j - N = a0 + o, shared with
-  // slice m+1, this slice is side 0) and left (j = a0 + o, shared with slice
-  // m-1, side 1)
-  const int rn0 = (N + a0 + 1) >> 1, rn1 = ((N + a0 + a.Mtr - 1) >> 1) + 1;
-  const int ln0 = (a0 + 1) >> 1, ln1 = ((a0 + a.Mtr - 1) >> 1) + 1;
-  auto each_right = [&](auto&& fn) {
-    for_range(rn0, rn1, [&](int n, float2 z) {
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int j = 2 * n + h;
-        const int o = j - N - a0;
-        if (o > 0 && o < a.Mtr) fn(o, tpos_of(j), weighted(j, h ? z.y : z.x));
-      }
-    });
-  };
-  auto each_left = [&](auto&& fn) {
-    for_range(ln0, ln1, [&](int n, float2 z) {
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int j = 2 * n + h;
-        const int o = j - a0;
-        if (o > 0 && o < a.Mtr) fn(o, tpos_of(j), weighted(j, h ? z.y : z.x));
-      }
-    });
-  };
-  ola_combine(a, tr0 + m, 0, rank, &s_flag, out, n32, each_right);
-  ola_combine(a, tr0 + (m + Sc - 1) % Sc, 1, rank, &s_flag, out, n32, each_left);
+  }
   // no remote shared-memory access after the exchange inside fourstep()
+}
+
+// Overlap-add of the transitions: output sample t = mN + a0 + o (o = 1..M-1,
+// t < L) of row s's clip is side 0 (slice m) + side 1 (slice m + 1).  A
+// thread takes offsets 4i .. 4i + 3 (16-byte patch loads; o = 0 is not a
+// transition sample).
+__global__ void __launch_bounds__(256) slice_ola_kernel(SliceArgs a, int64_t slice_base) {
+  const int o0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int64_t s = slice_base + blockIdx.y;
+  if (o0 >= a.Mtr) return;
+  int64_t sig_off;
+  int n32, L32, m;
+  row_of(a, s, sig_off, n32, L32, m);
+  const int64_t slot = a.rows ? a.rows[s].tr_base + m : s;
+  const float* p = a.ola_patch + slot * 2 * (int64_t)a.ola_stride;  // 16-byte aligned rows
+  const float4 x0 = __ldcs(reinterpret_cast<const float4*>(p + o0));
+  const float4 x1 = __ldcs(reinterpret_cast<const float4*>(p + a.ola_stride + o0));
+  const float v[4] = {x0.x + x1.x, x0.y + x1.y, x0.z + x1.z, x0.w + x1.w};
+  const int t0 = m * a.N + ((a.N - a.Mtr) >> 1) + o0;  // < L: the transition ends before the clip
+  float* out = a.out + sig_off;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const int o = o0 + q;
+    if (o >= 1 && o < a.Mtr && t0 + q < n32) out[t0 + q] = v[q];
+  }
 }
 
 template <int LOGP, int LOGQ>
@@ -490,7 +471,7 @@ SliceArgs make_args(const slicq_plan* pl, const Workspace& ws, int64_t n) {
   a.twband = pl->d_twband;
   a.tw4 = pl->d_tw4;
   a.ola_patch = ws.ola_patch;
-  a.ola_cnt = ws.ola_cnt;
+  a.ola_stride = (a.Mtr + 3) & ~3;
   return a;
 }
 
@@ -513,6 +494,22 @@ cudaError_t launch_slice_inverse(const slicq_plan* pl, int64_t n, int64_t batch,
   a.rows = rows;
   a.adjoint = kind == kSynthAdjoint;
   return dispatch(false, pl, a, batch * ws.S, st);
+}
+
+cudaError_t launch_slice_ola(const slicq_plan* pl, int64_t n, int64_t batch, const Workspace& ws, float* out,
+                             cudaStream_t st, const RowDesc* rows) {
+  SliceArgs a = make_args(pl, ws, n);
+  a.out = out;
+  a.rows = rows;
+  const int64_t total = batch * ws.S;
+  const unsigned bx = (unsigned)((a.Mtr + 1023) / 1024);  // 4 offsets per thread
+  for (int64_t s0 = 0; s0 < total; s0 += kMaxGridY) {
+    dim3 grid(bx, (unsigned)(total - s0 < kMaxGridY ? total - s0 : kMaxGridY));
+    slice_ola_kernel<<<grid, 256, 0, st>>>(a, s0);
+    const cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
 }
 
 }  // namespace slicq

@@ -208,7 +208,7 @@ class SliCQPlan:
         return buf[: n.value].copy()
 
     KERNEL_NAMES = ("slice_forward", "band_analysis", "band_synthesis", "slice_inverse",
-                    "band_boundary")
+                    "band_boundary", "slice_ola")
 
     def trace(self, enable: bool = True):
         """Start (or stop) recording CUDA events around every kernel launch."""

@@ -63,6 +63,7 @@ SMALL = [
     (48000.0, 50.0, 22000.0, 96, 4096, 1024, 20000, 1),    # ~90 widened channels cross DC
     (48000.0, 50.0, 22000.0, 24, 16384, 4096, 60000, 1),   # Nyquist plateau of M = 2048
     (48000.0, 50.0, 20000.0, 24, 16384, 4096, 50000, 2),   # Nyquist plateau of M = 4096
+    (44100.0, 50.0, 22050.0, 12, 4096, 1026, 20000, 2),    # transition = 2 mod 4, odd a0
 ]
 
 
