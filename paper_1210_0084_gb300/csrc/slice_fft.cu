@@ -240,9 +240,10 @@ __global__ void __launch_bounds__(kSliceMaxThreads, 2) slice_forward_kernel(Slic
 
   // the band analysis that follows in the same stream counts its work items from 0
   if (blockIdx.x == 0 && threadIdx.x == 0) *a.items = 0ull;
+  // the tables are first read in pass 2 of the column DFTs: the barrier after
+  // pass 1 covers the staging, so the input loads start right away
   const SliceTables tabs = stage_twiddles<LOGP, LOGQ>(a, sm);
   const SmemTwiddles& tws = tabs.tw;
-  __syncthreads();
   const int Pc = 1 << a.logPc;
   {
     float2 res[TQ::HELD];
