@@ -323,7 +323,9 @@ def main():
             step()
         torch.cuda.synchronize()
 
-    plan.trace(True)
+    # the timed steps run without the per-kernel trace: its events between
+    # launches would serialise kernels that otherwise overlap their start-up
+    # with the previous kernel's tail (programmatic dependent launch)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     if world > 1:
@@ -337,6 +339,12 @@ def main():
     torch.cuda.synchronize()
     if world > 1:
         dist.barrier()
+    # per-kernel times: the same number of steps again with the trace on
+    plan.trace(True)
+    for i in range(args.steps):
+        flush.fill_(i & 255)
+        step()
+    torch.cuda.synchronize()
     traced = plan.trace_read()
     plan.trace(False)
     # a second second of load, so that short timed regions still get samples

@@ -171,6 +171,7 @@ __device__ void analysis_persistent(const BandArgs& a, const GroupDesc& gd, int 
     for (int i = 2 * t; i < gd.fp_len; i += 2 * (int)blockDim.x) cp_async16(dst + i, src + i);
   };
   int64_t s = lane;
+  pdl_wait();  // the slice spectra of the previous kernel
   if (s < total) stage(s, s_x0);
   cp_async_commit();
   for (int it = 0; s < total; s += lanes, ++it) {
@@ -240,6 +241,7 @@ __device__ void analysis_persistent(const BandArgs& a, const GroupDesc& gd, int 
 __global__ void __launch_bounds__(kBandThreads, 1) band_analysis_persistent_kernel(
     BandArgs a, const int2* __restrict__ cta_map, const int* __restrict__ lanes_of) {
   extern __shared__ float2 sm[];
+  pdl_launch_dependents();
   const int2 gl = cta_map[blockIdx.x];  // (group, lane)
   const GroupDesc gd = a.groups[gl.x];
   const int lanes = lanes_of[gl.x];
@@ -412,6 +414,7 @@ __device__ void synthesis_two_pass(const BandArgs& a, const GroupDesc& gd, int k
       }
   };
   int64_t s = lane;
+  pdl_wait();  // the coefficients (and the previous kernel's use of the workspace)
   if (active && s < total) fetch(opaque(), s);
   cp_async_commit();
   __syncthreads();  // twiddles staged, layers zeroed
@@ -489,6 +492,7 @@ __device__ void synthesis_three_pass(const BandArgs& a, const GroupDesc& gd, int
   const ChannelLayers cl(bd, gd, lay, acc_n);
   const float* __restrict__ gw = a.win + bd.win_off;
   zero_layers(lay, nl * acc_n);  // the transform's first barrier orders this
+  pdl_wait();
   for (int64_t s = lane; s < total; s += lanes) {
     const float2* c = a.coef + s * a.cps + bd.coef_off;
     auto in = [&](int idx) { return __ldcs(c + idx); };
@@ -513,6 +517,7 @@ __device__ void synthesis_three_pass(const BandArgs& a, const GroupDesc& gd, int
 __global__ void __launch_bounds__(kBandThreads, 1) band_synthesis_persistent_kernel(
     BandArgs a, const int2* __restrict__ cta_map, const int* __restrict__ lanes_of) {
   extern __shared__ __align__(16) float2 sm[];
+  pdl_launch_dependents();
   const int2 gl = cta_map[blockIdx.x];  // (group, lane)
   const GroupDesc gd = a.groups[gl.x];
   const int lanes = lanes_of[gl.x];
@@ -542,9 +547,11 @@ __global__ void __launch_bounds__(kBandThreads, 1) band_synthesis_persistent_ker
 constexpr int kBoundarySlices = 4;
 
 __global__ void __launch_bounds__(256) band_boundary_kernel(BandArgs a, int64_t total) {
+  pdl_launch_dependents();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int h = i < a.ovl_total ? __ldg(a.ovl_bin + i) : 0;
+  pdl_wait();
   if (i >= a.ovl_total) return;
-  const int h = __ldg(a.ovl_bin + i);
   const int64_t s0 = (a.slice_base + blockIdx.y) * kBoundarySlices;
   float2 p0[kBoundarySlices], p1[kBoundarySlices];
 #pragma unroll
@@ -591,9 +598,8 @@ cudaError_t launch_band_analysis(const slicq_plan* pl, const Workspace& ws, int6
   cudaError_t e = cudaFuncSetAttribute(band_analysis_persistent_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, pl->band_smem_p);
   if (e != cudaSuccess) return e;
-  band_analysis_persistent_kernel<<<pl->n_cta_a, kBandThreads, pl->band_smem_p, st>>>(
-      a, pl->d_cta_map_a, pl->d_lanes_a);
-  return cudaGetLastError();
+  return launch_pdl(band_analysis_persistent_kernel, dim3(pl->n_cta_a), dim3(kBandThreads),
+                    (size_t)pl->band_smem_p, st, a, (const int2*)pl->d_cta_map_a, (const int*)pl->d_lanes_a);
 }
 
 cudaError_t launch_band_synthesis(const slicq_plan* pl, const float2* coef, int64_t batch,
@@ -606,9 +612,8 @@ cudaError_t launch_band_synthesis(const slicq_plan* pl, const float2* coef, int6
   cudaError_t e = cudaFuncSetAttribute(band_synthesis_persistent_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, pl->band_smem_s);
   if (e != cudaSuccess) return e;
-  band_synthesis_persistent_kernel<<<pl->n_cta_s, kBandThreads, pl->band_smem_s, st>>>(
-      a, pl->d_cta_map_s, pl->d_lanes_s);
-  return cudaGetLastError();
+  return launch_pdl(band_synthesis_persistent_kernel, dim3(pl->n_cta_s), dim3(kBandThreads),
+                    (size_t)pl->band_smem_s, st, a, (const int2*)pl->d_cta_map_s, (const int*)pl->d_lanes_s);
 }
 
 cudaError_t launch_band_boundaries(const slicq_plan* pl, int64_t batch, const Workspace& ws,
@@ -620,8 +625,7 @@ cudaError_t launch_band_boundaries(const slicq_plan* pl, int64_t batch, const Wo
   for (int64_t c0 = 0; c0 < chunks; c0 += kMaxGridY) {
     a.slice_base = c0;
     dim3 grid((unsigned)((pl->ovl_total + 255) / 256), (unsigned)(chunks - c0 < kMaxGridY ? chunks - c0 : kMaxGridY));
-    band_boundary_kernel<<<grid, 256, 0, st>>>(a, total);
-    const cudaError_t e = cudaGetLastError();
+    const cudaError_t e = launch_pdl(band_boundary_kernel, grid, dim3(256), 0, st, a, total);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

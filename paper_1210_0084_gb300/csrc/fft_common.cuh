@@ -14,6 +14,18 @@
 
 namespace slicq {
 
+// ------------------------------------------- programmatic dependent launch ---
+// Every hot kernel is launched with programmatic stream serialisation: it
+// lets the next kernel in the stream start launching (its CTAs fill SMs this
+// grid's tail leaves idle and stage their plan tables), and waits for the
+// previous kernel to finish (its writes visible) before it touches any
+// workspace, input or output memory.  Without the launch attribute both are
+// no-ops.
+__device__ __forceinline__ void pdl_launch_dependents() {
+  asm volatile("griddepcontrol.launch_dependents;\n" ::: "memory");
+}
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;\n" ::: "memory"); }
+
 // ---------------------------------------------------------------- complex ---
 __device__ __forceinline__ float2 c_add(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 c_sub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }

@@ -330,8 +330,8 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
     pl->tw_lb = (ilog2_64(L2) + 1) / 2;
     pl->slice_tw_off = std::max(std::max(cs1, xs1), std::max(cs3, zs3));
     const int ntw = (1 << pl->tw_lb) + (int)(L2 >> pl->tw_lb);
-    // + the pass-2 tables of lengths P and Q
-    pl->slice_smem = (pl->slice_tw_off + ntw + P + Qn) * (int)sizeof(float2);
+    // + the pass-2 tables of lengths P and Q and exp(-pi i v / Q), v < Q
+    pl->slice_smem = (pl->slice_tw_off + ntw + P + 2 * Qn) * (int)sizeof(float2);
   }
   return SLICQ_OK;
 }
@@ -541,8 +541,11 @@ void calibrate_lanes(slicq_plan* pl) {
     const int64_t rows = run == 0 ? per : S;
     workspace_layout_rows(pl, rows, work, &ws);
     long long* c = d_cyc + (size_t)std::max(run - 1, 0) * 2 * ncta;
-    ok = launch_band_analysis(pl, ws, 1, coef, 0, c) == cudaSuccess &&
-         launch_band_synthesis(pl, coef, 1, kSynthInverse, ws, 0, c + ncta) == cudaSuccess;
+    // each kernel alone on the device: a kernel started early under
+    // programmatic dependent launch would count its wait as work
+    ok = launch_band_analysis(pl, ws, 1, coef, 0, c) == cudaSuccess && cudaDeviceSynchronize() == cudaSuccess &&
+         launch_band_synthesis(pl, coef, 1, kSynthInverse, ws, 0, c + ncta) == cudaSuccess &&
+         cudaDeviceSynchronize() == cudaSuccess;
   }
   ok = ok && cudaDeviceSynchronize() == cudaSuccess;
   std::vector<long long> cyc(2 * (size_t)ncta * kRuns, 0);

@@ -42,6 +42,7 @@ struct SliceArgs {
   const float2* __restrict__ h0;  // h_0 over the slice as pairs (h_0[2e], h_0[2e+1])
   TwiddleTables tw;               // global two-level tables (copied to shared memory)
   const float2* __restrict__ twband;  // pass-2 tables of lengths 16..1024, [r][j] per length
+  const float2* __restrict__ tw4096;  // exp(-2 pi i t / 4096), t < 4096
   const float2* __restrict__ tw4; // four-step twiddles exp(-2 pi i q u / N) at [u Q + q]
   int tw_off;                     // shared-memory offset (float2) of the table copy
   float* ola_patch;               // [slice][2][ola_stride]: the two sides of each transition
@@ -104,7 +105,8 @@ struct PassTw {
 };
 
 // Shared-memory copies: the two-level table exp(-2 pi i t / 2N) at tw_off,
-// then the pass-2 tables of lengths P and Q (caller synchronises).
+// then the pass-2 tables of lengths P and Q and exp(-pi i v / Q), v < Q
+// (caller synchronises).
 struct SliceTables {
   SmemTwiddles tw;
   const float2* twP;
@@ -120,10 +122,13 @@ __device__ __forceinline__ SliceTables stage_twiddles(const SliceArgs& a, float2
   const int nhi = (2 * a.N) >> a.tw.lb;
   float2* tp = hi + nhi;
   float2* tq = tp + P;
+  float2* th = tq + Q;
   for (int i = threadIdx.x; i < nlo; i += blockDim.x) lo[i] = __ldg(a.tw.lo + i);
   for (int i = threadIdx.x; i < nhi; i += blockDim.x) hi[i] = __ldg(a.tw.hi + i);
   for (int i = threadIdx.x; i < P; i += blockDim.x) tp[i] = __ldg(a.twband + (P - 16) + i);
   for (int i = threadIdx.x; i < Q; i += blockDim.x) tq[i] = __ldg(a.twband + (Q - 16) + i);
+  // e^{-pi i v / Q} = e^{-2 pi i (v 2048 / Q) / 4096}, v < Q (Q <= 2048)
+  for (int i = threadIdx.x; i < Q; i += blockDim.x) th[i] = __ldg(a.tw4096 + i * (2048 / Q));
   return SliceTables{SmemTwiddles{lo, hi, a.tw.lb}, tp, tq};
 }
 
@@ -207,6 +212,7 @@ __global__ void __launch_bounds__(kSliceMaxThreads, 2) slice_forward_kernel(Slic
   using G = Geo<LOGP, LOGQ>;
   using TQ = typename G::TQ;
   extern __shared__ float2 sm[];
+  pdl_launch_dependents();
   cg::cluster_group cluster = cg::this_cluster();
   const int64_t s = blockIdx.x / a.C;
   int64_t sig_off;
@@ -238,12 +244,13 @@ __global__ void __launch_bounds__(kSliceMaxThreads, 2) slice_forward_kernel(Slic
     return x;
   };
 
-  // the band analysis that follows in the same stream counts its work items from 0
-  if (blockIdx.x == 0 && threadIdx.x == 0) *a.items = 0ull;
   // the tables are first read in pass 2 of the column DFTs: the barrier after
   // pass 1 covers the staging, so the input loads start right away
   const SliceTables tabs = stage_twiddles<LOGP, LOGQ>(a, sm);
   const SmemTwiddles& tws = tabs.tw;
+  pdl_wait();  // the input (and the previous kernel's use of the workspace)
+  // the band analysis that follows in the same stream counts its work items from 0
+  if (blockIdx.x == 0 && threadIdx.x == 0) *a.items = 0ull;
   const int Pc = 1 << a.logPc;
   {
     float2 res[TQ::HELD];
@@ -261,29 +268,32 @@ __global__ void __launch_bounds__(kSliceMaxThreads, 2) slice_forward_kernel(Slic
   }
   cluster.sync();
 
-  // X[k], k = u + P v for this CTA's rows u; X[N] from k = 0
+  // X[k], k = u + P v for this CTA's rows u; X[N] from k = 0.  A thread keeps
+  // one row u (fixed: idx & (Pc - 1) with blockDim a multiple of Pc), so its
+  // partner row P - u (row 0 for u = 0), the partner's CTA and e^{-2 pi i u / 2N}
+  // are computed once; e^{-2 pi i k / 2N} = e^{-2 pi i u / 2N} e^{-pi i v / Q}.
   const int rank = (int)cluster.block_rank();
   float2* X = a.spec + s * a.spec_stride;
-  const int held = Pc * G::Q;
+  const int ul = threadIdx.x & (Pc - 1);
+  const int u = rank * Pc + ul;
+  const int up = u == 0 ? 0 : G::P - u;
+  const float2* psm = cluster.map_shared_rank(sm, up >> a.logPc) + (up & (Pc - 1));
+  const float2 wu = tws((uint32_t)u);
+  const float2* thalf = tabs.twQ + G::Q;  // e^{-pi i v / Q}, v < Q (staged after the Q table)
+  const int vstep = (int)blockDim.x >> a.logPc;
   // unrolled so that several partner loads from distributed shared memory
   // are in flight at once
 #pragma unroll 8
-  for (int idx = threadIdx.x; idx < held; idx += blockDim.x) {
-    const int ul = idx & (Pc - 1);
-    const int v = idx >> a.logPc;
-    const int u = rank * Pc + ul;
-    const int k = u + G::P * v;
-    int up, vp;
-    if (u == 0) { up = 0; vp = (G::Q - v) & (G::Q - 1); }
-    else { up = G::P - u; vp = G::Q - 1 - v; }
-    const float2* rsm = cluster.map_shared_rank(sm, up >> a.logPc);
-    const float2 zp = c_conj(rsm[vp * Pc + (up & (Pc - 1))]);
+  for (int v = (int)threadIdx.x >> a.logPc; v < G::Q; v += vstep) {
+    const int vp = u == 0 ? ((G::Q - v) & (G::Q - 1)) : G::Q - 1 - v;
+    const float2 zp = c_conj(psm[vp * Pc]);
     const float2 z = sm[v * Pc + ul];
     // even part E = (Z[k] + conj Z[N-k]) / 2, odd part O = (Z[k] - conj Z[N-k]) / 2i
     const float2 E = c_scale(c_add(z, zp), 0.5f);
     const float2 D = c_sub(z, zp);
     const float2 O = make_float2(0.5f * D.y, -0.5f * D.x);
-    X[k] = c_add(E, c_mul(tws((uint32_t)k), O));
+    const int k = u + G::P * v;
+    X[k] = c_add(E, c_mul(c_mul(wu, thalf[v]), O));
     if (k == 0) X[a.N] = c_sub(E, O);
   }
   // keep this CTA's shared memory alive until its neighbours' partner loads
@@ -299,6 +309,7 @@ __global__ void __launch_bounds__(kSliceMaxThreads, 2) slice_inverse_kernel(Slic
   using G = Geo<LOGP, LOGQ>;
   using TQ = typename G::TQ;
   extern __shared__ float2 sm[];
+  pdl_launch_dependents();
   cg::cluster_group cluster = cg::this_cluster();
   const int64_t s = blockIdx.x / a.C;
   int64_t sig_off;
@@ -309,11 +320,12 @@ __global__ void __launch_bounds__(kSliceMaxThreads, 2) slice_inverse_kernel(Slic
   const float2* H = a.spec + s * a.spec_stride;
   const int N = a.N;
 
+  const SliceTables tabs = stage_twiddles<LOGP, LOGQ>(a, sm);
+  const SmemTwiddles& tws = tabs.tw;
+  pdl_wait();  // the synthesised spectra
   // the band synthesis of the next call counts its work items from 0 (it has
   // finished for this call: it precedes this kernel in the stream)
   if (blockIdx.x == 0 && threadIdx.x == 0) *a.items = 0ull;
-  const SliceTables tabs = stage_twiddles<LOGP, LOGQ>(a, sm);
-  const SmemTwiddles& tws = tabs.tw;
   __syncthreads();
   // Z[k] = (H[k] + conj H[N-k]) + i e^{+2 pi i k / 2N} (H[k] - conj H[N-k])
   auto load = [&](int k) -> float2 {
@@ -395,6 +407,8 @@ __global__ void __launch_bounds__(kSliceMaxThreads, 2) slice_inverse_kernel(Slic
 // thread takes offsets 4i .. 4i + 3 (16-byte patch loads; o = 0 is not a
 // transition sample).
 __global__ void __launch_bounds__(256) slice_ola_kernel(SliceArgs a, int64_t slice_base) {
+  pdl_launch_dependents();
+  pdl_wait();
   const int o0 = 4 * (blockIdx.x * blockDim.x + threadIdx.x);
   const int64_t s = slice_base + blockIdx.y;
   if (o0 >= a.Mtr) return;
@@ -427,13 +441,15 @@ cudaError_t launch_slice(bool forward, const slicq_plan* pl, const SliceArgs& a,
   cfg.blockDim = dim3(threads);
   cfg.dynamicSmemBytes = pl->slice_smem;
   cfg.stream = st;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = pl->C;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
+  attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;  // see pdl_wait
+  attr[1].val.programmaticStreamSerializationAllowed = 1;
   cfg.attrs = attr;
-  cfg.numAttrs = 1;
+  cfg.numAttrs = 2;
   e = cudaLaunchKernelEx(&cfg, kern, a);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
@@ -470,6 +486,7 @@ SliceArgs make_args(const slicq_plan* pl, const Workspace& ws, int64_t n) {
   a.tw = TwiddleTables{pl->d_tw_lo, pl->d_tw_hi, pl->tw_lb};
   a.tw_off = pl->slice_tw_off;
   a.twband = pl->d_twband;
+  a.tw4096 = pl->d_tw4096;
   a.tw4 = pl->d_tw4;
   a.ola_patch = ws.ola_patch;
   a.ola_stride = (a.Mtr + 3) & ~3;
@@ -506,8 +523,7 @@ cudaError_t launch_slice_ola(const slicq_plan* pl, int64_t n, int64_t batch, con
   const unsigned bx = (unsigned)((a.Mtr + 1023) / 1024);  // 4 offsets per thread
   for (int64_t s0 = 0; s0 < total; s0 += kMaxGridY) {
     dim3 grid(bx, (unsigned)(total - s0 < kMaxGridY ? total - s0 : kMaxGridY));
-    slice_ola_kernel<<<grid, 256, 0, st>>>(a, s0);
-    const cudaError_t e = cudaGetLastError();
+    const cudaError_t e = launch_pdl(slice_ola_kernel, grid, dim3(256), 0, st, a, s0);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
