@@ -18,6 +18,8 @@
 // of its layers in a fixed order.  Bins shared with the neighbouring group go
 // to two patch rows that a second kernel adds (a + b): the result is
 // deterministic without atomics.
+#include <algorithm>
+
 #include "fft_common.cuh"
 #include "internal.h"
 
@@ -588,6 +590,17 @@ BandArgs make_args(const slicq_plan* pl, const Workspace& ws, const float* win) 
 }
 
 }  // namespace
+
+int band_ctas_per_sm(const slicq_plan* pl, bool synthesis) {
+  int n = 0;
+  const void* k = synthesis ? (const void*)band_synthesis_persistent_kernel
+                            : (const void*)band_analysis_persistent_kernel;
+  const int smem = synthesis ? pl->band_smem_s : pl->band_smem_p;
+  if (cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess ||
+      cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, kBandThreads, smem) != cudaSuccess)
+    return 1;
+  return std::max(1, n);
+}
 
 cudaError_t launch_band_analysis(const slicq_plan* pl, const Workspace& ws, int64_t batch,
                                  float2* coef, cudaStream_t st, long long* cycles) {

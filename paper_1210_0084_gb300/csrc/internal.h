@@ -12,7 +12,9 @@
 namespace slicq {
 
 // Threads of one band-group CTA, and complex values each thread holds.
-constexpr int kBandThreads = 256;
+// 128 threads keep a group's shared memory and registers small enough for
+// two CTAs per SM, whose barriers do not wait on each other.
+constexpr int kBandThreads = 128;
 constexpr int kPerThread = 32;
 constexpr int kMaxTwoPassLog2 = 10;  // M_k <= 1024: two register passes of <= 32
 constexpr int kMaxBandLog2 = 12;     // M_k <= 4096: three passes (16, 16, <= 16)
@@ -107,6 +109,8 @@ struct slicq_plan {
   int band_in_a = 0;      // complex values per staged analysis input (max footprint)
   int band_in_s = 0;      // complex values per staged synthesis input (max group block)
   int num_sms = 152;      // SMs of the plan's device (grid sizing)
+  int slots_a = 152;      // CTAs the persistent band analysis runs (SMs x CTAs per SM)
+  int slots_s = 152;      // CTAs the persistent band synthesis runs
   int band_smem_p = 0;    // dynamic shared memory of the persistent band analysis (bytes)
   int n_cta_a = 0;        // CTAs of the persistent band analysis
   int n_cta_s = 0;        // CTAs of the persistent band synthesis
@@ -192,6 +196,10 @@ cudaError_t launch_band_synthesis(const slicq_plan* pl, const float2* coef,
                                   int64_t batch, SynthKind kind,
                                   const Workspace& ws, cudaStream_t st,
                                   long long* cycles = nullptr);
+// CTAs of the persistent band analysis (synthesis) one SM holds at the
+// plan's shared-memory sizes.
+int band_ctas_per_sm(const slicq_plan* pl, bool synthesis);
+
 // Adds the two partial sums of the bins shared by neighbouring band groups
 // (after launch_band_synthesis, before launch_slice_inverse).
 cudaError_t launch_band_boundaries(const slicq_plan* pl, int64_t batch, const Workspace& ws,

@@ -523,7 +523,8 @@ cudaError_t upload_lanes(slicq_plan* pl, bool synthesis, const std::vector<int>&
 void calibrate_lanes(slicq_plan* pl) {
   constexpr int kRuns = 3;
   const int G = pl->G;
-  const int per = std::max(1, pl->num_sms / G);
+  // the same lanes per group for both kernels, within both kernels' slots
+  const int per = std::max(1, std::min(pl->slots_a, pl->slots_s) / G);
   const std::vector<int> equal(G, per);
   const int64_t S = 6 * (int64_t)per;
   Workspace ws;
@@ -570,8 +571,8 @@ void calibrate_lanes(slicq_plan* pl) {
   cudaFree(coef);
   cudaFree(d_cyc);
   // measured costs when the runs succeeded, the estimates otherwise
-  upload_lanes(pl, false, balance_lanes(pl->cost_a, pl->num_sms));
-  upload_lanes(pl, true, balance_lanes(pl->cost_s, pl->num_sms));
+  upload_lanes(pl, false, balance_lanes(pl->cost_a, pl->slots_a));
+  upload_lanes(pl, true, balance_lanes(pl->cost_s, pl->slots_s));
 }
 
 }  // namespace
@@ -592,9 +593,9 @@ slicq_status build_tables(slicq_plan* pl) {
   const size_t o_ga = take(sizeof(float) * (pl->win_total + 32));  // + padding
   const size_t o_gs = take(sizeof(float) * (pl->win_total + 32));  // + padding
   const size_t o_gadj = take(sizeof(float) * (pl->win_total + 32));  // + padding
-  // persistent band kernels: one CTA per SM in total (at least one per
-  // group), lanes (CTAs) per group chosen so that the estimated time of a
-  // lane, cost / lanes, is as even as possible
+  // persistent band kernels: as many CTAs as the SMs hold at once (at least
+  // one per group), lanes (CTAs) per group chosen so that the estimated time
+  // of a lane, cost / lanes, is as even as possible
   {
     int sms = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl->device) == cudaSuccess && sms > 0)
@@ -602,12 +603,14 @@ slicq_status build_tables(slicq_plan* pl) {
   }
   // (these estimates from the group sizes are replaced by measured costs in
   // calibrate_lanes once the tables exist)
-  std::vector<int> lanes_a = balance_lanes(pl->cost_a, pl->num_sms);
-  std::vector<int> lanes_s = balance_lanes(pl->cost_s, pl->num_sms);
+  pl->slots_a = pl->num_sms * band_ctas_per_sm(pl, false);
+  pl->slots_s = pl->num_sms * band_ctas_per_sm(pl, true);
+  std::vector<int> lanes_a = balance_lanes(pl->cost_a, pl->slots_a);
+  std::vector<int> lanes_s = balance_lanes(pl->cost_s, pl->slots_s);
   std::vector<int2> map_a = lane_map(lanes_a), map_s = lane_map(lanes_s);
   pl->n_cta_a = (int)map_a.size();
   pl->n_cta_s = (int)map_s.size();
-  const size_t map_cap = (size_t)std::max(pl->G, pl->num_sms);  // sum of lanes at most
+  const size_t map_cap = (size_t)std::max(pl->G, std::max(pl->slots_a, pl->slots_s));  // sum of lanes at most
   const size_t o_map_a = take(sizeof(int2) * map_cap);
   const size_t o_lanes_a = take(sizeof(int) * pl->G);
   const size_t o_map_s = take(sizeof(int2) * map_cap);
