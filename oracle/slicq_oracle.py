@@ -31,7 +31,9 @@ R3  g_0 and g_{K+1} are flat (value 1) on their open supports of width
 R4  H is zero on the closed complement of ]-1/2, 1/2[ (strict support).
 R5  The lower bound on the filter length (Sec. 5.2) widens Omega_k to
     min_filter_len * xi_s / L for k = 1..K, keeping the centre.
-R6  M_k = L/a_k = max(16, next power of two >= |J_k|) (pow2 policy).
+R6  M_k = L/a_k = max(16, next power of two >= |J_k|) (pow2 policy); the
+    const policy (the rectangular representation, Sec. 4.1) gives every
+    channel the largest of these.
 R7  The configured "slice length" is 2N and the "transition" is M (< N).
 R8  Tukey slicing window h_0(d), d = j - N, with u = clip((|d|-(N-M)/2)/M, 0, 1)
     and h_0 = cos^2(pi u / 2) for |d| < (N+M)/2, 0 otherwise.
@@ -46,7 +48,8 @@ R12 Real signals keep channels 0..K+1; the dropped channels are the complex
 
 Parity status: every public function is pinned by a test under ``tests/``
 (brute-force atoms, explicit frame operator, perfect reconstruction, tight
-frame energy, adjoint identity, closed forms of Table 1, partition of unity).
+frame energy, adjoint identity, closed forms of Table 1, partition of unity,
+time and frequency localisation of the sliCQ spectrogram).
 """
 
 from __future__ import annotations
@@ -65,7 +68,7 @@ __all__ = [
     "nsgt_analysis", "nsgt_synthesis", "slicq_slices", "slicq_forward",
     "slicq_inverse", "slicq_adjoint", "slicq_forward_complex",
     "slicq_inverse_complex", "atoms", "frame_operator_matrix",
-    "num_slices", "padded_length", "two_layer_view",
+    "num_slices", "padded_length", "two_layer_view", "slicq_spectrogram",
 ]
 
 # ---------------------------------------------------------------------------
@@ -564,3 +567,12 @@ def two_layer_view(coef: np.ndarray, plan: SliCQPlan, k: int) -> np.ndarray:
         idx = (np.arange(M) + (m - 1) * M // 2) % total
         s[m % 2, idx] = coef[m, o:o + M]
     return s
+
+
+def slicq_spectrogram(coef: np.ndarray, plan: SliCQPlan) -> np.ndarray:
+    """sliCQ spectrogram |s^0 + s^1|^2 (Sec. 4.1): the two layers of the
+    2-layer array summed, squared magnitude, for the kept channels
+    k = 0..K+1 concatenated (channel k's S M_k / 2 time indices start at
+    S off_k / 2)."""
+    return np.concatenate([np.abs(two_layer_view(coef, plan, k).sum(axis=0)) ** 2
+                           for k in range(plan.real_channels)])

@@ -229,6 +229,8 @@ def _slicq_params_cases():
         (O.SliCQParams(44100.0, 50.0, 22050.0, 12, 8192, 2048), 30001),   # ragged tail
         (O.SliCQParams(16000.0, 50.0, 8000.0, 24, 2048, 512), 2048),      # S = 2
         (O.SliCQParams(1000.0, 40.0, 500.0, 4, 128, 16, min_filter_len=4), 1000),
+        # rectangular representation: one M for every channel (Sec. 4.1)
+        (O.SliCQParams(16000.0, 50.0, 8000.0, 24, 2048, 512, mk_policy="const"), 5000),
     ]
 
 
@@ -372,3 +374,61 @@ def test_two_layer_view_places_every_coefficient_once():
     assert np.isclose(np.abs(s).sum(), np.abs(c[:, o:o + M]).sum())
     assert s[1, 0] == c[1, o]        # slice 1 starts at n = 0 of layer 1
     assert s[0, 0] == c[0, o + M // 2]   # slice 0 starts at -M/2 (circular)
+
+
+def test_rectangular_representation_has_one_band_length():
+    """Sec. 4.1: with L/a_k constant the coefficients of a slice form a
+    (K+2) x M array; M is a power of two >= every |J_k|, so it divides 2N."""
+    p = O.SliCQParams(16000.0, 50.0, 8000.0, 24, 2048, 512, mk_policy="const")
+    plan = O.make_plan(p)
+    M = set(int(m) for m in plan.M)
+    assert len(M) == 1
+    (m,) = M
+    assert m & (m - 1) == 0 and p.slice_len % m == 0
+    assert m >= max(len(ch.g) for ch in plan.sys.channels)
+    assert plan.coefs_per_slice == m * plan.real_channels
+
+
+# ------------------------------------------------------- sliCQ spectrogram ---
+
+def _channel_blocks(spec, plan, S):
+    blocks, o = [], 0
+    for k in range(plan.real_channels):
+        n = S * int(plan.M[k]) // 2
+        blocks.append(spec[o:o + n])
+        o += n
+    assert o == spec.shape[0]
+    return blocks
+
+
+def test_spectrogram_localises_an_impulse_in_time():
+    """An impulse at sample t0 peaks, in channel k, at time index t0 / a_k
+    (a_k = 2N / M_k): slice m's coefficient n sits at time (m-1)N + n a_k
+    (Algorithm 3 with the slice's first sample as time origin), which the
+    2-layer array places at n + (m-1) M_k / 2 (Sec. 4.1)."""
+    p = O.SliCQParams(16000.0, 50.0, 8000.0, 24, 2048, 512)
+    plan = O.make_plan(p)
+    n = 16384
+    S = O.num_slices(n, p.slice_len)
+    for t0 in (5000, 9100):
+        f = np.zeros(n)
+        f[t0] = 1.0
+        blocks = _channel_blocks(O.slicq_spectrogram(O.slicq_forward(f, plan), plan), plan, S)
+        for k in range(plan.real_channels - 12, plan.real_channels - 1):  # short atoms
+            a = p.slice_len // int(plan.M[k])
+            peak = int(np.argmax(blocks[k]))
+            assert abs(peak * a - t0) <= a, (k, peak, t0)
+
+
+def test_spectrogram_localises_a_tone_in_frequency():
+    """A sinusoid at xi_{k0} has the largest mean spectrogram value in
+    channel k0 (Sec. 3: g_k is centred at xi_k)."""
+    p = O.SliCQParams(44100.0, 50.0, 22050.0, 12, 8192, 2048)
+    plan = O.make_plan(p)
+    n = 32768
+    S = O.num_slices(n, p.slice_len)
+    t = np.arange(n) / p.fs
+    for k0 in (40, 75):
+        f = np.sin(2 * np.pi * plan.sys.xi[k0] * t + 0.7)
+        blocks = _channel_blocks(O.slicq_spectrogram(O.slicq_forward(f, plan), plan), plan, S)
+        assert int(np.argmax([b.mean() for b in blocks])) == k0
