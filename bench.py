@@ -39,7 +39,7 @@ WORKLOAD = dict(fs=44100.0, fmin=32.7, fmax=22050.0, bins_per_octave=48, slice_l
 WORKLOAD_NAME = ("60 s stereo 44.1 kHz, pink noise + 20 decaying harmonic tones; Hann CQ windows "
                  "B=48, fmin=32.7 Hz, fmax=22050 Hz; slice 2N=65536, transition 16384")
 KERNELS = ("slice_forward", "band_analysis", "band_synthesis", "band_boundary", "slice_inverse",
-           "slice_ola")
+           "slice_ola", "spectrogram")
 
 
 def _env_int(name, default):
@@ -374,7 +374,8 @@ def main():
     # samples two slices share)
     alg_bytes = {"slice_forward": batch * n * 4, "band_analysis": batch * S * cps * 8,
                  "band_synthesis": batch * S * cps * 8, "band_boundary": 0,
-                 "slice_inverse": batch * n * 4, "slice_ola": 0}
+                 "slice_inverse": batch * n * 4, "slice_ola": 0,
+                 "spectrogram": batch * S * cps * 10}
     peak, peak_kind = _peaks()
     kern = {}
     for k in KERNELS:

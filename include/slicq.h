@@ -62,7 +62,11 @@ typedef enum {
 } slicq_status;
 
 typedef enum { SLICQ_WIN_HANN = 0 } slicq_window;          /* H of Sec. 3 */
-typedef enum { SLICQ_MK_POW2 = 0 } slicq_mk_policy;         /* M_k choice */
+typedef enum {                                             /* M_k choice */
+  SLICQ_MK_POW2 = 0,   /* M_k = max(16, next power of two >= |J_k|) */
+  SLICQ_MK_MULT4 = 1,  /* smallest multiple of 4 >= |J_k|: not built (EUNSUPPORTED) */
+  SLICQ_MK_CONST = 2   /* one M for every channel: the rectangular representation */
+} slicq_mk_policy;
 
 /*
  * Parameters of one sliCQ system (Sec. 3 and Sec. 4).
@@ -77,6 +81,9 @@ typedef enum { SLICQ_MK_POW2 = 0 } slicq_mk_policy;         /* M_k choice */
  *                    16 is the paper's recommendation). >= 1.
  *   window           SLICQ_WIN_HANN.
  *   mk_policy        SLICQ_MK_POW2: M_k = max(16, next power of two >= |J_k|).
+ *                    SLICQ_MK_CONST: every M_k is the largest of those, so
+ *                    each slice's coefficients form a (K+2) x M array (the
+ *                    rectangular representation, L/a_k constant, Sec. 4.1).
  *   slice_cluster    CTAs per slice FFT (thread-block cluster size); 0 picks
  *                    the default.  Must be a power of two <= 8 if given.
  */
@@ -233,6 +240,25 @@ SLICQ_API slicq_status slicq_batch_forward(const slicq_batch* batch, const float
 SLICQ_API slicq_status slicq_batch_inverse(const slicq_batch* batch, const float* d_coef,
                                            float* d_sig_out, void* d_work, size_t work_bytes,
                                            cudaStream_t stream);
+
+/*
+ * sliCQ spectrogram (Sec. 4.1): |s^0 + s^1|^2, where the 2-layer array s^l
+ * holds slice m's coefficient n of channel k in layer l = m mod 2 at time
+ * index t = n + (m-1) M_k / 2 (circular in S M_k / 2), i.e. at time
+ * t a_k, a_k = 2N / M_k.  Each t is covered by one even and one odd slice.
+ *   d_coef        device, complex64 [batch][S][coefs_per_slice] as written
+ *                 by slicq_forward for (n_samples, batch); 8-byte aligned.
+ *   d_out         device, float32 [batch][S * coefs_per_slice / 2]: channel
+ *                 k's S M_k / 2 values (t = 0, 1, ...) start at S off_k / 2
+ *                 (off_k as returned by slicq_layout_tables).
+ *   out_capacity  floats available at d_out.
+ * Asynchronous on `stream`; allocates nothing, needs no workspace.
+ * Errors: SLICQ_EINVAL (null pointers, n_samples or batch < 1, misaligned
+ * d_coef), SLICQ_ESIZE (out_capacity too small), SLICQ_ECUDA.
+ */
+SLICQ_API slicq_status slicq_spectrogram(const slicq_plan* plan, const float* d_coef, int64_t n_samples,
+                                         int64_t batch, float* d_out, int64_t out_capacity,
+                                         cudaStream_t stream);
 
 /*
  * Forward sliCQ without a caller workspace and without allocating (the paper

@@ -75,7 +75,7 @@ size_t workspace_layout(const slicq_plan* pl, int64_t n, int64_t batch, void* ba
   auto take = [&](size_t bytes) { const size_t o = off; off = align256(off + bytes); return o; };
   const size_t o_items = take(2 * sizeof(unsigned long long));
   const size_t o_spec = take(sizeof(float2) * slices * w.spec_stride);
-  const size_t o_bp = take(sizeof(float2) * slices * 2 * std::max(pl->ovl_total, 1));
+  const size_t o_bp = take(sizeof(float2) * slices * std::max(pl->ovl_total, 1));
   const size_t o_op = take(sizeof(float) * slices * 2 * ((pl->params.trans_len + 3) & ~int64_t(3)));
   w.bytes = off;
   if (base) {
@@ -98,7 +98,7 @@ size_t workspace_layout_rows(const slicq_plan* pl, int64_t rows, void* base, Wor
   auto take = [&](size_t bytes) { const size_t o = off; off = align256(off + bytes); return o; };
   const size_t o_items = take(2 * sizeof(unsigned long long));
   const size_t o_spec = take(sizeof(float2) * rows * w.spec_stride);
-  const size_t o_bp = take(sizeof(float2) * rows * 2 * std::max(pl->ovl_total, 1));
+  const size_t o_bp = take(sizeof(float2) * rows * std::max(pl->ovl_total, 1));
   const size_t o_op = take(sizeof(float) * rows * 2 * ((pl->params.trans_len + 3) & ~int64_t(3)));
   w.bytes = off;
   if (base) {
@@ -241,7 +241,7 @@ static slicq_status synthesis(const slicq_plan* plan, const float* d_coef, int64
   return on_device(plan, [&] {
     cudaError_t e = traced(plan, 2, stream, [&] {
       return launch_band_synthesis(plan, reinterpret_cast<const float2*>(d_coef), batch, kind, ws, stream); });
-    if (e == cudaSuccess && plan->ovl_total > 0)
+    if (e == cudaSuccess && !plan->shared.empty())
       e = traced(plan, 4, stream, [&] { return launch_band_boundaries(plan, batch, ws, stream); });
     if (e == cudaSuccess)
       e = traced(plan, 3, stream, [&] {
@@ -260,6 +260,19 @@ slicq_status slicq_inverse(const slicq_plan* plan, const float* d_coef, int64_t 
 slicq_status slicq_adjoint(const slicq_plan* plan, const float* d_coef, int64_t n_samples, int64_t batch,
                            float* d_out, void* d_work, size_t work_bytes, cudaStream_t stream) {
   return synthesis(plan, d_coef, n_samples, batch, d_out, d_work, work_bytes, stream, kSynthAdjoint);
+}
+
+slicq_status slicq_spectrogram(const slicq_plan* plan, const float* d_coef, int64_t n_samples, int64_t batch,
+                               float* d_out, int64_t out_capacity, cudaStream_t stream) {
+  if (!plan || !d_coef || !d_out || n_samples < 1 || batch < 1) return SLICQ_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(d_coef) & 7) != 0) return SLICQ_EINVAL;
+  const int64_t S = slicq_num_slices(plan, n_samples);
+  if (S * plan->N >= (int64_t(1) << 31)) return SLICQ_EUNSUPPORTED;  // positions are 32-bit
+  if (out_capacity < batch * S * (plan->coefs_per_slice / 2)) return SLICQ_ESIZE;
+  return on_device(plan, [&] {
+    return from_cuda(traced(plan, 6, stream, [&] {
+      return launch_spectrogram(plan, reinterpret_cast<const float2*>(d_coef), S, batch, d_out, stream); }));
+  });
 }
 
 slicq_status slicq_plan_table(const slicq_plan* plan, int32_t which, float* h_out, int64_t count,

@@ -33,10 +33,9 @@ namespace {
 struct BandArgs {
   const BandDesc* __restrict__ bands;
   const GroupDesc* __restrict__ groups;
-  const BoundaryDesc* __restrict__ bounds;
   const int16_t* __restrict__ thread_band;
-  const int32_t* __restrict__ ovl_start;    // [G] boundary offsets in a patch row
-  const int32_t* __restrict__ ovl_bin;      // [ovl_total] bin of each patch-row entry
+  const int32_t* __restrict__ slot_base;    // [N+1] patch slot of bin h for group g: slot_base[h] + g
+  const int4* __restrict__ shared;          // bins of several groups: (h, first slot, count, 0)
   const float* __restrict__ win;     // window table of this launch
   const float2* __restrict__ twband; // pass-2 twiddle tables of lengths 16..1024 (2032 entries)
   const float2* __restrict__ tw4096; // exp(-2 pi i t / 4096), t < 4096 (three-pass lengths)
@@ -46,7 +45,7 @@ struct BandArgs {
   int64_t spec_stride;
   float2* coef;                      // [slice][cps]
   int64_t cps;
-  float2* patch;                     // [slice][2][ovl_total]
+  float2* patch;                     // [slice][ovl_total] partial sums of shared bins
   int ovl_total;
   int N;
   long long* cycles;                 // optional: SM clocks of each CTA (plan calibration)
@@ -283,26 +282,24 @@ __device__ __forceinline__ void zero_layers(float2* p, int n) {
   if ((n & 1) && threadIdx.x == 0) p[n - 1] = make_float2(0.f, 0.f);
 }
 
-// Where slice s's bins of the group go: the spectrum row, or the patch rows
-// for bins shared with a neighbouring group (side 0: the lower group of a
-// boundary, side 1: the upper one).
+// Where slice s's bins of group g go: the spectrum row, or, for a bin other
+// groups also cover, the group's slot of that bin in the slice's patch row.
 struct BinSink {
   float2* spec;
-  float2* patch_l;
-  float2* patch_r;
-  int ex_lo, ex_hi;
-  __device__ __forceinline__ BinSink(const BandArgs& a, const GroupDesc& gd, int64_t s) {
+  float2* row;
+  const int32_t* __restrict__ slot;
+  int g, ex_lo, ex_hi;
+  __device__ __forceinline__ BinSink(const BandArgs& a, const GroupDesc& gd, int gi, int64_t s) {
     spec = a.spec + s * a.spec_stride;
-    float2* row = a.patch + s * 2 * (int64_t)a.ovl_total;
-    patch_l = gd.left_bd >= 0 ? row + a.ovl_total + a.ovl_start[gd.left_bd] - gd.acc_lo : nullptr;
-    patch_r = gd.right_bd >= 0 ? row + a.ovl_start[gd.right_bd] - gd.ex_hi : nullptr;
+    row = a.patch + s * (int64_t)a.ovl_total;
+    slot = a.slot_base;
+    g = gi;
     ex_lo = gd.ex_lo;
     ex_hi = gd.ex_hi;
   }
   __device__ __forceinline__ void put(int h, float2 v) const {
-    if (h < ex_lo) patch_l[h] = v;
-    else if (h >= ex_hi) patch_r[h] = v;
-    else spec[h] = v;
+    if (h >= ex_lo && h < ex_hi) spec[h] = v;
+    else row[__ldg(slot + h) + g] = v;
   }
 };
 
@@ -357,7 +354,7 @@ struct ChannelLayers {
 };
 
 template <int LOGM>
-__device__ void synthesis_two_pass(const BandArgs& a, const GroupDesc& gd, int k, int lane, int lanes,
+__device__ void synthesis_two_pass(const BandArgs& a, const GroupDesc& gd, int gi, int k, int lane, int lanes,
                                    int64_t total, float2* sm) {
   using T = Team<LOGM>;
   constexpr int M = 1 << LOGM;
@@ -468,7 +465,7 @@ __device__ void synthesis_two_pass(const BandArgs& a, const GroupDesc& gd, int k
       }
     }
     __syncthreads();
-    write_bins_n(gd, lay, nl, acc_n, BinSink(a, gd, s));
+    write_bins_n(gd, lay, nl, acc_n, BinSink(a, gd, gi, s));
   }
   cp_async_wait<0>();
 }
@@ -477,7 +474,7 @@ __device__ void synthesis_two_pass(const BandArgs& a, const GroupDesc& gd, int k
 // writes Y w g~ at the support offsets of its buffer; windows and twiddles
 // come from global memory (L1-resident).
 template <int LOGM>
-__device__ void synthesis_three_pass(const BandArgs& a, const GroupDesc& gd, int k, int lane, int lanes,
+__device__ void synthesis_three_pass(const BandArgs& a, const GroupDesc& gd, int gi, int k, int lane, int lanes,
                                      int64_t total, float2* sm) {
   constexpr int M = 1 << LOGM;
   const int t = threadIdx.x;
@@ -512,7 +509,7 @@ __device__ void synthesis_three_pass(const BandArgs& a, const GroupDesc& gd, int
       }
     }
     __syncthreads();
-    write_bins_n(gd, lay, nl, acc_n, BinSink(a, gd, s));
+    write_bins_n(gd, lay, nl, acc_n, BinSink(a, gd, gi, s));
   }
 }
 
@@ -527,15 +524,15 @@ __global__ void __launch_bounds__(kBandThreads, 1) band_synthesis_persistent_ker
   const int64_t total = a.total;
   const long long t0 = clock64();
   switch (gd.log2M) {
-    case 4: synthesis_two_pass<4>(a, gd, k, gl.y, lanes, total, sm); break;
-    case 5: synthesis_two_pass<5>(a, gd, k, gl.y, lanes, total, sm); break;
-    case 6: synthesis_two_pass<6>(a, gd, k, gl.y, lanes, total, sm); break;
-    case 7: synthesis_two_pass<7>(a, gd, k, gl.y, lanes, total, sm); break;
-    case 8: synthesis_two_pass<8>(a, gd, k, gl.y, lanes, total, sm); break;
-    case 9: synthesis_two_pass<9>(a, gd, k, gl.y, lanes, total, sm); break;
-    case 10: synthesis_two_pass<10>(a, gd, k, gl.y, lanes, total, sm); break;
-    case 11: synthesis_three_pass<11>(a, gd, k, gl.y, lanes, total, sm); break;
-    case 12: synthesis_three_pass<12>(a, gd, k, gl.y, lanes, total, sm); break;
+    case 4: synthesis_two_pass<4>(a, gd, gl.x, k, gl.y, lanes, total, sm); break;
+    case 5: synthesis_two_pass<5>(a, gd, gl.x, k, gl.y, lanes, total, sm); break;
+    case 6: synthesis_two_pass<6>(a, gd, gl.x, k, gl.y, lanes, total, sm); break;
+    case 7: synthesis_two_pass<7>(a, gd, gl.x, k, gl.y, lanes, total, sm); break;
+    case 8: synthesis_two_pass<8>(a, gd, gl.x, k, gl.y, lanes, total, sm); break;
+    case 9: synthesis_two_pass<9>(a, gd, gl.x, k, gl.y, lanes, total, sm); break;
+    case 10: synthesis_two_pass<10>(a, gd, gl.x, k, gl.y, lanes, total, sm); break;
+    case 11: synthesis_three_pass<11>(a, gd, gl.x, k, gl.y, lanes, total, sm); break;
+    case 12: synthesis_three_pass<12>(a, gd, gl.x, k, gl.y, lanes, total, sm); break;
   }
   if (a.cycles) {
     __syncthreads();
@@ -543,40 +540,40 @@ __global__ void __launch_bounds__(kBandThreads, 1) band_synthesis_persistent_ker
   }
 }
 
-// Bins shared by groups g and g + 1: spectrum = side 0 + side 1.  Thread i
-// takes the i-th bin of the concatenated boundaries (bin number from the
-// plan's table) in kBoundarySlices consecutive slices.
+// Bins covered by several groups: spectrum = the groups' partial sums in
+// group order.  Thread i takes the i-th shared bin in kBoundarySlices
+// consecutive slices.
 constexpr int kBoundarySlices = 4;
 
-__global__ void __launch_bounds__(256) band_boundary_kernel(BandArgs a, int64_t total) {
+__global__ void __launch_bounds__(256) band_boundary_kernel(BandArgs a, int nshared, int64_t total) {
   pdl_launch_dependents();
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  const int h = i < a.ovl_total ? __ldg(a.ovl_bin + i) : 0;
+  const int4 sb = i < nshared ? __ldg(a.shared + i) : make_int4(0, 0, 0, 0);
   pdl_wait();
-  if (i >= a.ovl_total) return;
+  if (i >= nshared) return;
   const int64_t s0 = (a.slice_base + blockIdx.y) * kBoundarySlices;
-  float2 p0[kBoundarySlices], p1[kBoundarySlices];
+  float2 v[kBoundarySlices];
 #pragma unroll
   for (int u = 0; u < kBoundarySlices; ++u) {
+    v[u] = make_float2(0.f, 0.f);
     if (s0 + u < total) {
-      const float2* row = a.patch + (s0 + u) * 2 * (int64_t)a.ovl_total;
-      p0[u] = __ldcs(row + i);
-      p1[u] = __ldcs(row + a.ovl_total + i);
+      const float2* row = a.patch + (s0 + u) * (int64_t)a.ovl_total + sb.y;
+      v[u] = __ldcs(row);
+      for (int j = 1; j < sb.z; ++j) v[u] = c_add(v[u], __ldcs(row + j));
     }
   }
 #pragma unroll
   for (int u = 0; u < kBoundarySlices; ++u)
-    if (s0 + u < total) a.spec[(s0 + u) * a.spec_stride + h] = c_add(p0[u], p1[u]);
+    if (s0 + u < total) a.spec[(s0 + u) * a.spec_stride + sb.x] = v[u];
 }
 
 BandArgs make_args(const slicq_plan* pl, const Workspace& ws, const float* win) {
   BandArgs a{};
   a.bands = pl->d_bands;
   a.groups = pl->d_groups;
-  a.bounds = pl->d_bounds;
   a.thread_band = pl->d_thread_band;
-  a.ovl_start = pl->d_ovl_start;
-  a.ovl_bin = pl->d_ovl_bin;
+  a.slot_base = pl->d_slot_base;
+  a.shared = pl->d_shared;
   a.win = win;
   a.twband = pl->d_twband;
   a.tw4096 = pl->d_tw4096;
@@ -631,14 +628,15 @@ cudaError_t launch_band_synthesis(const slicq_plan* pl, const float2* coef, int6
 
 cudaError_t launch_band_boundaries(const slicq_plan* pl, int64_t batch, const Workspace& ws,
                                    cudaStream_t st) {
-  if (pl->ovl_total == 0) return cudaSuccess;
+  const int nshared = (int)pl->shared.size();
+  if (nshared == 0) return cudaSuccess;
   BandArgs a = make_args(pl, ws, nullptr);
   const int64_t total = batch * ws.S;
   const int64_t chunks = (total + kBoundarySlices - 1) / kBoundarySlices;
   for (int64_t c0 = 0; c0 < chunks; c0 += kMaxGridY) {
     a.slice_base = c0;
-    dim3 grid((unsigned)((pl->ovl_total + 255) / 256), (unsigned)(chunks - c0 < kMaxGridY ? chunks - c0 : kMaxGridY));
-    const cudaError_t e = launch_pdl(band_boundary_kernel, grid, dim3(256), 0, st, a, total);
+    dim3 grid((unsigned)((nshared + 255) / 256), (unsigned)(chunks - c0 < kMaxGridY ? chunks - c0 : kMaxGridY));
+    const cudaError_t e = launch_pdl(band_boundary_kernel, grid, dim3(256), 0, st, a, nshared, total);
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;

@@ -48,17 +48,13 @@ constexpr int kNoPhase = 0xFFFF;
 struct GroupDesc {
   int32_t band_begin, band_end;  // channels [begin, end)
   int32_t acc_lo, acc_hi;        // half-spectrum bins the group touches
-  int32_t ex_lo, ex_hi;          // bins only this group touches
-  int32_t left_bd, right_bd;     // boundary indices, -1 if none
+  int32_t ex_lo, ex_hi;          // bins only this group touches (the others: patch slots)
+  int32_t pad0_, pad1_;
   int32_t log2M;                 // every channel of the group has M = 2^log2M
   int32_t fp_lo, fp_len;         // spectrum block the analysis stages (even bounds)
   int32_t nphases;               // direct layers (bits 0-15), mirrored layers (16-31)
 };
 
-// Bins [lo, hi) touched by two neighbouring groups (bd and bd + 1).
-struct BoundaryDesc {
-  int32_t lo, hi;
-};
 
 // One slice row of a ragged batch: the clip it belongs to and where that
 // clip's samples are (uniform batches compute the same from (row / S)).
@@ -102,8 +98,7 @@ struct slicq_plan {
   int logP = 0, logQ = 0; // four-step split of the N-point complex FFT
   int C = 1;              // cluster size of the slice kernels
   int G = 0;              // band groups
-  int max_ovl = 0;        // longest group-boundary overlap (bins)
-  int ovl_total = 0;      // bins of all group boundaries of one slice
+  int ovl_total = 0;      // patch slots of one slice: sum over shared bins of their group count
   int band_smem_a = 0;    // dynamic shared memory of band analysis (bytes)
   int band_smem_s = 0;    // dynamic shared memory of band synthesis (bytes)
   int band_in_a = 0;      // complex values per staged analysis input (max footprint)
@@ -122,9 +117,8 @@ struct slicq_plan {
 
   std::vector<slicq::BandDesc> bands;
   std::vector<slicq::GroupDesc> groups;
-  std::vector<slicq::BoundaryDesc> bounds;
-  std::vector<int32_t> ovl_start;    // [G] prefix sums of the boundary widths
-  std::vector<int32_t> ovl_bin;      // [ovl_total] bin of each entry of a patch row
+  std::vector<int32_t> slot_base;    // [N+1] patch slot of bin h for group g: slot_base[h] + g (-1: one group)
+  std::vector<int4> shared;          // bins of several groups: (h, first slot, group count, 0)
   std::vector<int16_t> thread_band;  // [G][kBandThreads] channel or -1
   std::vector<double> xi, omega;     // Table 1, channels 0..K+1
   std::vector<int64_t> jlo;          // unwrapped first support sample
@@ -133,9 +127,9 @@ struct slicq_plan {
   void* d_arena = nullptr;
   slicq::BandDesc* d_bands = nullptr;
   slicq::GroupDesc* d_groups = nullptr;
-  slicq::BoundaryDesc* d_bounds = nullptr;
-  int32_t* d_ovl_start = nullptr;  // [G]: prefix sums of the boundary widths
-  int32_t* d_ovl_bin = nullptr;    // [ovl_total]: bin of each entry of a patch row
+  int32_t* d_slot_base = nullptr;  // slot_base on the device
+  int4* d_shared = nullptr;        // shared on the device
+  int2* d_half_chan = nullptr;     // [coefs_per_slice / 2]: (off_k, log2 M_k) of each half-coefficient
   int16_t* d_thread_band = nullptr;
   float* d_ga = nullptr;    // g_k / sqrt(2N)
   float* d_gs = nullptr;    // w_k g~_k / sqrt(2N)
@@ -176,7 +170,7 @@ struct Workspace {
   unsigned long long* items = nullptr;  // [2] work counters of the band kernels
   int64_t spec_stride = 0;         // complex values per slice spectrum row
   float2* spec = nullptr;          // [batch * S][spec_stride]
-  float2* band_patch = nullptr;    // [batch * S][G - 1][2][max_ovl]
+  float2* band_patch = nullptr;    // [batch * S][ovl_total]: partial sums of shared bins
   float* ola_patch = nullptr;      // [batch * S][2][M rounded up to 4]: the two sides of each transition
   size_t bytes = 0;
 };
@@ -208,6 +202,10 @@ cudaError_t launch_slice_inverse(const slicq_plan* pl, int64_t n,
                                  int64_t batch, SynthKind kind,
                                  const Workspace& ws, float* out,
                                  cudaStream_t st, const RowDesc* rows = nullptr);
+// sliCQ spectrogram |s^0 + s^1|^2 of coefficients [batch][S][coefs_per_slice].
+cudaError_t launch_spectrogram(const slicq_plan* pl, const float2* coef, int64_t S, int64_t batch,
+                               float* out, cudaStream_t st);
+
 // Adds the two sides of every transition into the output (after
 // launch_slice_inverse).
 cudaError_t launch_slice_ola(const slicq_plan* pl, int64_t n, int64_t batch,

@@ -39,7 +39,9 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
   if (!(p->fs > 0) || !(p->fmin > 0) || !(p->fmax > p->fmin) || p->bins_per_octave < 1 ||
       p->min_filter_len < 1 || !std::isfinite(p->fs) || !std::isfinite(p->fmax))
     return SLICQ_EINVAL;
-  if (p->window != SLICQ_WIN_HANN || p->mk_policy != SLICQ_MK_POW2) return SLICQ_EINVAL;
+  if (p->window != SLICQ_WIN_HANN) return SLICQ_EINVAL;
+  if (p->mk_policy == SLICQ_MK_MULT4) return SLICQ_EUNSUPPORTED;  // band FFTs are radix-2
+  if (p->mk_policy != SLICQ_MK_POW2 && p->mk_policy != SLICQ_MK_CONST) return SLICQ_EINVAL;
   const int64_t L2 = p->slice_len;
   if (!is_pow2(L2)) return SLICQ_EINVAL;
   if (L2 < 2048 || L2 > 131072) return SLICQ_EUNSUPPORTED;
@@ -79,25 +81,42 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
   int64_t coef_off = 0, win_off = 0;
   std::vector<int> foot_lo(nch), foot_hi(nch);
   std::vector<int32_t> cover(N + 2, 0);
-  for (int k = 0; k < nch; ++k) {
+  auto support = [&](int k, int64_t& first, int64_t& count) -> bool {
     const double centre = pl->xi[k] * (double)L2 / p->fs;
     const double half = pl->omega[k] * (double)L2 / (2.0 * p->fs);
     const int64_t lo = (int64_t)std::floor(centre - half) - 1;
     const int64_t hi = (int64_t)std::ceil(centre + half) + 1;
-    int64_t first = 0, count = 0;
+    first = 0;
+    count = 0;
     for (int64_t j = lo; j <= hi; ++j) {
       const double t = ((double)j * p->fs / (double)L2 - pl->xi[k]) / pl->omega[k];
       if (std::fabs(t) < 0.5) {
         if (count == 0) first = j;
-        if (j != first + count) return SLICQ_EINVAL;  // support must be an interval
+        if (j != first + count) return false;  // support must be an interval
         ++count;
       }
     }
-    if (count == 0) {  // degenerate plateau: no bin; keep a zero window of one bin
-      first = (int64_t)std::llround(centre);
+    if (count == 0) first = (int64_t)std::llround(centre);  // degenerate plateau: a zero window of one bin
+    return true;
+  };
+  // rectangular representation: every M_k is the largest pow2 length
+  int64_t const_M = 0;
+  if (p->mk_policy == SLICQ_MK_CONST) {
+    int64_t widest = 0;
+    for (int k = 0; k < nch; ++k) {
+      int64_t first, count;
+      if (!support(k, first, count)) return SLICQ_EINVAL;
+      widest = std::max(widest, count);
     }
+    const_M = 16;
+    while (const_M < widest) const_M <<= 1;
+  }
+  for (int k = 0; k < nch; ++k) {
+    int64_t first = 0, count = 0;
+    if (!support(k, first, count)) return SLICQ_EINVAL;
     int64_t M = 16;
     while (M < count) M <<= 1;
+    if (const_M) M = const_M;
     if (M > L2) return SLICQ_EINVAL;
     if (M > (int64_t(1) << kMaxBandLog2)) return SLICQ_EUNSUPPORTED;
     BandDesc& bd = pl->bands[k];
@@ -258,46 +277,43 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
   }
   const int G = (int)pl->groups.size();
   pl->G = G;
-  // ---- boundaries between neighbouring groups
-  pl->bounds.clear();
-  pl->max_ovl = 1;
-  for (int g = 0; g < G; ++g) pl->groups[g].left_bd = pl->groups[g].right_bd = -1;
+  // ---- bins covered by more than one group.  Groups are ordered and their
+  // ranges [acc_lo, acc_hi) move monotonically, so the groups covering a bin
+  // are a contiguous run first(h) .. first(h) + count(h) - 1.  A shared bin
+  // gets one patch slot per covering group, in group order: group g writes
+  // its partial sum of bin h to slot slot_base[h] + g of the slice's row.
   for (int g = 0; g + 1 < G; ++g) {
-    GroupDesc& a = pl->groups[g];
-    GroupDesc& b = pl->groups[g + 1];
+    const GroupDesc& a = pl->groups[g];
+    const GroupDesc& b = pl->groups[g + 1];
     if (b.acc_lo < a.acc_lo || b.acc_hi < a.acc_hi) return SLICQ_EUNSUPPORTED;
-    if (b.acc_lo > a.acc_hi) return SLICQ_EINVAL;  // uncovered bins
-    if (g + 2 < G && pl->groups[g + 2].acc_lo < a.acc_hi) return SLICQ_EUNSUPPORTED;
-    if (b.acc_lo < a.acc_hi) {
-      BoundaryDesc bd{b.acc_lo, a.acc_hi};
-      a.right_bd = b.left_bd = (int)pl->bounds.size();
-      pl->bounds.push_back(bd);
-      pl->max_ovl = std::max(pl->max_ovl, bd.hi - bd.lo);
-    }
   }
-  // every boundary slot is [g][g+1] indexed by g: remap to group index
-  {
-    std::vector<BoundaryDesc> byg(std::max(G - 1, 1), BoundaryDesc{0, 0});
-    for (int g = 0; g + 1 < G; ++g) {
-      if (pl->groups[g].right_bd >= 0) byg[g] = pl->bounds[pl->groups[g].right_bd];
-      pl->groups[g].right_bd = pl->groups[g].right_bd >= 0 ? g : -1;
-      pl->groups[g + 1].left_bd = pl->groups[g].right_bd;
-    }
-    pl->bounds = byg;
-  }
-  // boundary g's bins are [ovl_start[g], ovl_start[g + 1]) of a slice's patch row
-  pl->ovl_start.assign(std::max(G, 1), 0);
-  for (int g = 0; g + 1 < G; ++g)
-    pl->ovl_start[g + 1] = pl->ovl_start[g] + (pl->bounds[g].hi - pl->bounds[g].lo);
-  pl->ovl_total = pl->ovl_start[std::max(G, 1) - 1];
-  pl->ovl_bin.clear();
-  for (int g = 0; g + 1 < G; ++g)
-    for (int h = pl->bounds[g].lo; h < pl->bounds[g].hi; ++h) pl->ovl_bin.push_back(h);
   if (pl->groups.front().acc_lo != 0 || pl->groups.back().acc_hi != N + 1) return SLICQ_EINVAL;
+  {
+    std::vector<int32_t> first(N + 1, -1), count(N + 1, 0);
+    for (int g = 0; g < G; ++g)
+      for (int h = pl->groups[g].acc_lo; h < pl->groups[g].acc_hi; ++h) {
+        if (first[h] < 0) first[h] = g;
+        ++count[h];
+      }
+    pl->slot_base.assign(N + 1, -1);
+    pl->shared.clear();
+    int32_t off = 0;
+    for (int h = 0; h <= N; ++h) {
+      if (count[h] == 0) return SLICQ_EINVAL;  // eq. painlessframe1: every bin is covered
+      if (count[h] > 1) {
+        pl->slot_base[h] = off - first[h];
+        pl->shared.push_back(make_int4(h, off, count[h], 0));
+        off += count[h];
+      }
+    }
+    pl->ovl_total = off;
+  }
+  // bins of group g that no other group covers: [ex_lo, ex_hi)
   for (int g = 0; g < G; ++g) {
     GroupDesc& gd = pl->groups[g];
-    gd.ex_lo = gd.left_bd >= 0 ? pl->bounds[gd.left_bd].hi : gd.acc_lo;
-    gd.ex_hi = gd.right_bd >= 0 ? pl->bounds[gd.right_bd].lo : gd.acc_hi;
+    gd.ex_lo = g > 0 ? std::max(gd.acc_lo, pl->groups[g - 1].acc_hi) : gd.acc_lo;
+    gd.ex_hi = g + 1 < G ? std::min(gd.acc_hi, pl->groups[g + 1].acc_lo) : gd.acc_hi;
+    if (gd.ex_hi < gd.ex_lo) gd.ex_hi = gd.ex_lo;
   }
   pl->band_in_a = (in_a + 1) & ~1;
   pl->band_in_s = (in_s + 1) & ~1;
@@ -586,10 +602,16 @@ slicq_status build_tables(slicq_plan* pl) {
   auto take = [&](size_t bytes) { const size_t o = off; off = align256(off + bytes); return o; };
   const size_t o_bands = take(sizeof(BandDesc) * nch);
   const size_t o_groups = take(sizeof(GroupDesc) * pl->G);
-  const size_t o_bounds = take(sizeof(BoundaryDesc) * pl->bounds.size());
   const size_t o_tb = take(sizeof(int16_t) * pl->thread_band.size());
-  const size_t o_ovl = take(sizeof(int32_t) * pl->ovl_start.size());
-  const size_t o_ovlb = take(sizeof(int32_t) * std::max<size_t>(pl->ovl_bin.size(), 1));
+  const size_t o_slot = take(sizeof(int32_t) * pl->slot_base.size());
+  const size_t o_shared = take(sizeof(int4) * std::max<size_t>(pl->shared.size(), 1));
+  // spectrogram: half-coefficient i of a slice -> (off_k, log2 M_k) of its channel
+  std::vector<int2> half(pl->coefs_per_slice / 2);
+  for (int k = 0; k < nch; ++k) {
+    const BandDesc& b = pl->bands[k];
+    for (int r = 0; r < (1 << (b.log2M - 1)); ++r) half[b.coef_off / 2 + r] = make_int2(b.coef_off, b.log2M);
+  }
+  const size_t o_half = take(sizeof(int2) * std::max<size_t>(half.size(), 1));
   const size_t o_ga = take(sizeof(float) * (pl->win_total + 32));  // + padding
   const size_t o_gs = take(sizeof(float) * (pl->win_total + 32));  // + padding
   const size_t o_gadj = take(sizeof(float) * (pl->win_total + 32));  // + padding
@@ -626,10 +648,10 @@ slicq_status build_tables(slicq_plan* pl) {
   char* base = (char*)pl->d_arena;
   pl->d_bands = (BandDesc*)(base + o_bands);
   pl->d_groups = (GroupDesc*)(base + o_groups);
-  pl->d_bounds = (BoundaryDesc*)(base + o_bounds);
   pl->d_thread_band = (int16_t*)(base + o_tb);
-  pl->d_ovl_start = (int32_t*)(base + o_ovl);
-  pl->d_ovl_bin = (int32_t*)(base + o_ovlb);
+  pl->d_slot_base = (int32_t*)(base + o_slot);
+  pl->d_shared = (int4*)(base + o_shared);
+  pl->d_half_chan = (int2*)(base + o_half);
   pl->d_ga = (float*)(base + o_ga);
   pl->d_gs = (float*)(base + o_gs);
   pl->d_gadj = (float*)(base + o_gadj);
@@ -656,17 +678,15 @@ slicq_status build_tables(slicq_plan* pl) {
   if (e == cudaSuccess)
     e = cudaMemcpy(pl->d_groups, pl->groups.data(), sizeof(GroupDesc) * pl->G, cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
-    e = cudaMemcpy(pl->d_bounds, pl->bounds.data(), sizeof(BoundaryDesc) * pl->bounds.size(),
-                   cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
     e = cudaMemcpy(pl->d_thread_band, pl->thread_band.data(),
                    sizeof(int16_t) * pl->thread_band.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
-    e = cudaMemcpy(pl->d_ovl_start, pl->ovl_start.data(), sizeof(int32_t) * pl->ovl_start.size(),
+    e = cudaMemcpy(pl->d_slot_base, pl->slot_base.data(), sizeof(int32_t) * pl->slot_base.size(),
                    cudaMemcpyHostToDevice);
-  if (e == cudaSuccess && !pl->ovl_bin.empty())
-    e = cudaMemcpy(pl->d_ovl_bin, pl->ovl_bin.data(), sizeof(int32_t) * pl->ovl_bin.size(),
-                   cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !pl->shared.empty())
+    e = cudaMemcpy(pl->d_shared, pl->shared.data(), sizeof(int4) * pl->shared.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess && !half.empty())
+    e = cudaMemcpy(pl->d_half_chan, half.data(), sizeof(int2) * half.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = upload_lanes(pl, false, lanes_a);
   if (e == cudaSuccess) e = upload_lanes(pl, true, lanes_s);

@@ -84,6 +84,7 @@ def load_library():
         "slicq_adjoint": (ctypes.c_int, [VP, VP, I64, I64, VP, VP, SZ, VP]),
         "slicq_plan_table": (ctypes.c_int, [VP, I32, VP, I64, ctypes.POINTER(I64)]),
         "slicq_trace_enable": (ctypes.c_int, [VP, I32]),
+        "slicq_spectrogram": (ctypes.c_int, [VP, VP, I64, I64, VP, I64, VP]),
         "slicq_batch_create": (ctypes.c_int, [VP, I32, VP, VP, I32, ctypes.POINTER(VP)]),
         "slicq_batch_destroy": (None, [VP]),
         "slicq_batch_layout": (ctypes.c_int, [VP, VP, VP, VP, ctypes.POINTER(I64), ctypes.POINTER(I64),
@@ -117,11 +118,13 @@ class SliCQParams:
     trans_len: int
     min_filter_len: int = 16
     slice_cluster: int = 0
+    mk_policy: str = "pow2"   # "pow2" or "const" (rectangular representation)
 
     def to_c(self) -> _Params:
+        mk = {"pow2": 0, "mult4": 1, "const": 2}[self.mk_policy]
         return _Params(float(self.fs), float(self.fmin), float(self.fmax),
                        int(self.bins_per_octave), int(self.min_filter_len),
-                       int(self.slice_len), int(self.trans_len), 0, 0,
+                       int(self.slice_len), int(self.trans_len), 0, mk,
                        int(self.slice_cluster), 0)
 
 
@@ -208,7 +211,7 @@ class SliCQPlan:
         return buf[: n.value].copy()
 
     KERNEL_NAMES = ("slice_forward", "band_analysis", "band_synthesis", "slice_inverse",
-                    "band_boundary", "slice_ola")
+                    "band_boundary", "slice_ola", "spectrogram")
 
     def trace(self, enable: bool = True):
         """Start (or stop) recording CUDA events around every kernel launch."""
@@ -275,6 +278,32 @@ class SliCQPlan:
     def adjoint(self, c, n: int, out=None):
         """Re(A^H c) [batch, n]: the gradient of the analysis map."""
         return self._synth(self.lib.slicq_adjoint, c, n, out, "slicq_adjoint")
+
+    def spectrogram(self, c, n: int, out=None):
+        """sliCQ spectrogram |s^0 + s^1|^2 (Sec. 4.1), float32
+        [batch, S * coefs_per_slice / 2]; channel k's S M_k / 2 time indices
+        start at S off_k / 2 (see ``spectrogram_blocks``)."""
+        t = self._torch
+        if c.dtype != t.complex64 or not c.is_cuda:
+            raise TypeError("expected complex64 CUDA coefficients")
+        squeeze = c.dim() == 2
+        c3 = (c.unsqueeze(0) if squeeze else c).contiguous()
+        batch = c3.shape[0]
+        S = self.num_slices(n)
+        if tuple(c3.shape[1:]) != (S, self.coefs_per_slice):
+            raise ValueError(f"coefficients must be [batch, {S}, {self.coefs_per_slice}]")
+        if out is None:
+            out = t.empty((batch, S * (self.coefs_per_slice // 2)), dtype=t.float32, device=c3.device)
+        _check(self.lib.slicq_spectrogram(self._h, c3.data_ptr(), int(n), batch, out.data_ptr(),
+                                          out.numel(), self._stream()), "slicq_spectrogram")
+        return out[0] if squeeze else out
+
+    def spectrogram_blocks(self, spec, n: int):
+        """Per-channel views [.., S M_k / 2] of a spectrogram from ``spectrogram``."""
+        lay = layout(self.params)
+        S = self.num_slices(n)
+        return [spec[..., S * int(o) // 2: S * (int(o) + int(m)) // 2]
+                for o, m in zip(lay["off"], lay["M"])]
 
 
 def _autograd():

@@ -47,14 +47,17 @@ CASES = [
     S.SliCQParams(22050.0, 50.0, 11025.0, 24, 16384, 4096),
     S.SliCQParams(44100.0, 40.0, 22050.0, 24, 8192, 2048),
     S.SliCQParams(16000.0, 50.0, 8000.0, 24, 2048, 512),
+    S.SliCQParams(16000.0, 50.0, 8000.0, 24, 2048, 512, mk_policy="const"),
+    S.SliCQParams(44100.0, 32.7, 22050.0, 48, 65536, 16384, mk_policy="const"),
 ]
 
 
-@pytest.mark.parametrize("p", CASES, ids=lambda p: f"fs{int(p.fs)}_B{p.bins_per_octave}_L{p.slice_len}")
+@pytest.mark.parametrize("p", CASES,
+                         ids=lambda p: f"fs{int(p.fs)}_B{p.bins_per_octave}_L{p.slice_len}_{p.mk_policy}")
 def test_host_layout_matches_oracle(lib, p):
     lay = S.layout(p)
     op = O.make_plan(O.SliCQParams(p.fs, p.fmin, p.fmax, p.bins_per_octave, p.slice_len,
-                                   p.trans_len, p.min_filter_len))
+                                   p.trans_len, p.min_filter_len, mk_policy=p.mk_policy))
     K = op.K
     assert lay["M"].shape[0] == K + 2
     chans = op.sys.channels[: K + 2]
@@ -72,6 +75,7 @@ def test_host_layout_matches_oracle(lib, p):
     (dict(trans_len=3), 1), (dict(trans_len=8192), 1), (dict(bins_per_octave=0), 1),
     (dict(slice_len=1024, trans_len=256), 6), (dict(slice_cluster=3), 1),
     (dict(fmin=23000.0, fmax=30000.0), 1),
+    (dict(mk_policy="mult4"), 6),   # mixed-radix band lengths are not built
 ])
 def test_invalid_parameters_are_rejected(lib, kw, code):
     base = dict(fs=44100.0, fmin=50.0, fmax=22050.0, bins_per_octave=12, slice_len=8192,
@@ -91,3 +95,4 @@ def test_null_pointers(lib):
     assert lib.slicq_forward(None, None, 1, 1, None, 0, None, 0, None) == 1
     assert lib.slicq_inverse(None, None, 1, 1, None, None, 0, None) == 1
     assert lib.slicq_adjoint(None, None, 1, 1, None, None, 0, None) == 1
+    assert lib.slicq_spectrogram(None, None, 1, 1, None, 0, None) == 1

@@ -35,7 +35,7 @@ def S():
 
 def _oplan(p):
     return O.make_plan(O.SliCQParams(p.fs, p.fmin, p.fmax, p.bins_per_octave, p.slice_len,
-                                     p.trans_len, p.min_filter_len))
+                                     p.trans_len, p.min_filter_len, mk_policy=p.mk_policy))
 
 
 def _rel(a, b):
@@ -64,19 +64,21 @@ SMALL = [
     (48000.0, 50.0, 22000.0, 24, 16384, 4096, 60000, 1),   # Nyquist plateau of M = 2048
     (48000.0, 50.0, 20000.0, 24, 16384, 4096, 50000, 2),   # Nyquist plateau of M = 4096
     (44100.0, 50.0, 22050.0, 12, 4096, 1026, 20000, 2),    # transition = 2 mod 4, odd a0
+    (16000.0, 50.0, 8000.0, 24, 2048, 512, 7000, 2, "const"),  # rectangular: one M_k
+    (44100.0, 50.0, 22050.0, 12, 8192, 2048, 30000, 1, "const"),
 ]
 
 
 def _params(S, c):
-    fs, fmin, fmax, B, L2, M, n, batch = c
-    return S.SliCQParams(fs, fmin, fmax, B, L2, M), n, batch
+    fs, fmin, fmax, B, L2, M, n, batch = c[:8]
+    return S.SliCQParams(fs, fmin, fmax, B, L2, M, mk_policy=c[8] if len(c) > 8 else "pow2"), n, batch
 
 
 def _signal(n, fs, batch, seed):
     return np.stack([signals.noise_plus_sines(n, fs, seed + i) for i in range(batch)])
 
 
-@pytest.mark.parametrize("case", SMALL, ids=lambda c: f"L{c[4]}_B{c[3]}_n{c[6]}x{c[7]}")
+@pytest.mark.parametrize("case", SMALL, ids=lambda c: f"L{c[4]}_B{c[3]}_n{c[6]}x{c[7]}" + ("_const" if len(c) > 8 else ""))
 def test_forward_inverse_adjoint_parity(S, case):
     p, n, batch = _params(S, case)
     plan = S.SliCQPlan(p)
@@ -217,3 +219,27 @@ def test_autograd_backward_is_adjoint(S):
     fm = np.sum(np.abs(O.slicq_forward(x64 - h * v, op)) ** 2)
     fd = (fp - fm) / (2 * h)
     assert abs(fd - float(np.dot(g, v))) <= 1e-4 * abs(fd)
+
+
+@pytest.mark.parametrize("case", [SMALL[0], SMALL[3], SMALL[7], SMALL[-2]],
+                         ids=["L2048", "L16384_B96", "L8192_DC", "L2048_const"])
+def test_spectrogram_parity(S, case):
+    """|s^0 + s^1|^2 (Sec. 4.1) of the GPU's coefficients against the oracle's
+    spectrogram of the same coefficients, and the per-channel blocks."""
+    p, n, batch = _params(S, case)
+    plan = S.SliCQPlan(p)
+    op = _oplan(p)
+    x = _signal(n, p.fs, batch, 300)
+    c = plan.forward(torch.from_numpy(x).cuda())
+    spec = plan.spectrogram(c, n)
+    torch.cuda.synchronize()
+    cg = c.cpu().numpy().astype(np.complex128)
+    got = spec.cpu().numpy()
+    for b in range(batch):
+        ref = O.slicq_spectrogram(cg[b], op)
+        assert got[b].shape == ref.shape
+        assert _rel(got[b], ref) <= REL
+        assert np.abs(got[b] - ref).max() <= ELEM * np.abs(ref).max()
+    blocks = plan.spectrogram_blocks(spec, n)
+    Sn = plan.num_slices(n)
+    assert [int(bl.shape[-1]) for bl in blocks] == [Sn * int(m) // 2 for m in op.M[: op.real_channels]]
