@@ -230,12 +230,13 @@ def run_reference(args, x, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def _config(world):
-    return {"workload": WORKLOAD_NAME, "fs": WORKLOAD["fs"], "bins_per_octave": WORKLOAD["bins_per_octave"],
+def _config(world, mk_policy="pow2"):
+    name = WORKLOAD_NAME + ("" if mk_policy == "pow2" else "; rectangular representation (one M_k)")
+    return {"workload": name, "fs": WORKLOAD["fs"], "bins_per_octave": WORKLOAD["bins_per_octave"],
             "fmin": WORKLOAD["fmin"], "fmax": WORKLOAD["fmax"], "slice_len": WORKLOAD["slice_len"],
             "trans_len": WORKLOAD["trans_len"], "channels": WORKLOAD["channels"],
             "samples_per_channel": WORKLOAD["seconds"] * int(WORKLOAD["fs"]),
-            "mk_policy": "pow2", "l2": "flushed between timed steps (256 MiB write, outside the events)",
+            "mk_policy": mk_policy, "l2": "flushed between timed steps (256 MiB write, outside the events)",
             "parallelism": f"replicas x{world} (independent clips, no exchange)"}
 
 
@@ -251,6 +252,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=10)
     ap.add_argument("--no-clock-load", action="store_true",
                     help="skip the 1 s load phases around the timed region (for profiler runs)")
+    ap.add_argument("--mk-policy", choices=("pow2", "const"), default="pow2",
+                    help="band lengths: pow2 (headline) or const (rectangular representation)")
     ap.add_argument("--workload", choices=("stereo60", "ragged"), default="stereo60",
                     help="stereo60: the headline workload; ragged: 256 clips over 16 plans "
                          "in one CUDA-graph replay per step")
@@ -288,7 +291,7 @@ def main():
     from paper_1210_0084_gb300.slicq import SliCQParams, SliCQPlan
 
     p = SliCQParams(WORKLOAD["fs"], WORKLOAD["fmin"], WORKLOAD["fmax"], WORKLOAD["bins_per_octave"],
-                    WORKLOAD["slice_len"], WORKLOAD["trans_len"])
+                    WORKLOAD["slice_len"], WORKLOAD["trans_len"], mk_policy=args.mk_policy)
     plan = SliCQPlan(p, local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(dev)
@@ -422,6 +425,29 @@ def main():
            "h2d_bytes_per_step": int(xh.numel() * 4), "d2h_bytes_per_step": int(yh.numel() * 4),
            "ms_per_step": float(e_ms_t.item()), "recon_rel_err": e2e_err}
 
+    # the sliCQ spectrogram |s0 + s1|^2 of the step's coefficients (Sec. 4.1):
+    # not part of the step; timed alone (reads every coefficient once, writes
+    # one float per two coefficients)
+    spec = torch.empty((batch, S * (cps // 2)), dtype=torch.float32, device=dev)
+    for _ in range(3):
+        plan.spectrogram(c, n, out=spec)
+    sp_ms = []
+    for i in range(10):
+        flush.fill_(i & 255)
+        s0 = torch.cuda.Event(enable_timing=True)
+        s1 = torch.cuda.Event(enable_timing=True)
+        s0.record(stream)
+        plan.spectrogram(c, n, out=spec)
+        s1.record(stream)
+        torch.cuda.synchronize()
+        sp_ms.append(s0.elapsed_time(s1))
+    sp_bytes = batch * S * cps * 10
+    sp_avg = statistics.median(sp_ms)
+    epilogues = {"spectrogram": {"ms": sp_avg, "alg_bytes": sp_bytes,
+                                 "gbs": sp_bytes / (sp_avg * 1e-3) / 1e9,
+                                 "frac": sp_bytes / (sp_avg * 1e-3) / 1e9 / peak,
+                                 "bound": "hbm", "peak_kind": f"of {peak_kind}"}}
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(x)
@@ -431,8 +457,8 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": _config(world), "recon_rel_err": recon_err,
-            "roofline": roofline, "step_roofline": step_roof, "kernels": kern,
+            "config": _config(world, args.mk_policy), "recon_rel_err": recon_err,
+            "roofline": roofline, "step_roofline": step_roof, "kernels": kern, "epilogues": epilogues,
             "gpu_launches": len(traced), "e2e": e2e, "cpu_baseline": cpu,
             "clocks": sampler.summary(), "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms),
         }
