@@ -89,6 +89,8 @@ class SliCQParams:
     mk_policy       'pow2' (reading R6), 'mult4' (smallest multiple of 4 that
                     is >= |J_k|) or 'const' (one M for all channels: the
                     rectangular representation of Sec. 6)
+    window          'hann' (Sec. 3) or 'blackman_harris' (4-term, Harris 1978;
+                    the alternative the paper's experiments mention)
     """
 
     fs: float
@@ -99,6 +101,7 @@ class SliCQParams:
     trans_len: int
     min_filter_len: int = 16
     mk_policy: str = "pow2"
+    window: str = "hann"
 
     @property
     def N(self) -> int:
@@ -190,6 +193,28 @@ def _hann(t: np.ndarray) -> np.ndarray:
     return np.where(np.abs(t) < 0.5, np.cos(np.pi * t) ** 2, 0.0)
 
 
+# 4-term Blackman-Harris window (F. J. Harris, "On the use of windows for
+# harmonic analysis with the discrete Fourier transform", Proc. IEEE 66(1),
+# 1978): a0 - a1 cos(2 pi x) + a2 cos(4 pi x) - a3 cos(6 pi x) on x in [0, 1],
+# here centred (x = t + 1/2), which flips the signs of the odd terms.
+_BH = (0.35875, 0.48829, 0.14128, 0.01168)
+
+
+def _blackman_harris(t: np.ndarray) -> np.ndarray:
+    """H(t) = sum_i a_i cos(2 pi i t) on ]-1/2, 1/2[, zero outside (the
+    alternative window of Sec. 5.3; strict support as reading R4)."""
+    w = sum(a * np.cos(2 * np.pi * i * t) for i, a in enumerate(_BH))
+    return np.where(np.abs(t) < 0.5, w, 0.0)
+
+
+def _window(t: np.ndarray, shape: str) -> np.ndarray:
+    if shape == "hann":
+        return _hann(t)
+    if shape == "blackman_harris":
+        return _blackman_harris(t)
+    raise ValueError(shape)
+
+
 def _next_pow2(n: int) -> int:
     return 1 << max(0, int(n - 1).bit_length())
 
@@ -233,7 +258,7 @@ def nsg_system(p: SliCQParams, L: Optional[int] = None) -> NSGSystem:
         if k in (0, K + 1):
             vals = np.ones(j.shape[0])
         else:
-            vals = _hann(t)
+            vals = _window(t, p.window)
         raw.append((int(j[0]) if j.size else int(round(centre)), vals))
         const_M = max(const_M, vals.shape[0])
     if p.mk_policy == "const":

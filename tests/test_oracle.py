@@ -432,3 +432,49 @@ def test_spectrogram_localises_a_tone_in_frequency():
         f = np.sin(2 * np.pi * plan.sys.xi[k0] * t + 0.7)
         blocks = _channel_blocks(O.slicq_spectrogram(O.slicq_forward(f, plan), plan), plan, S)
         assert int(np.argmax([b.mean() for b in blocks])) == k0
+
+
+# ---------------------------------------------------- Blackman-Harris window ---
+
+BH = O.SliCQParams(44100.0, 50.0, 22050.0, 12, 8192, 2048, window="blackman_harris")
+
+
+def test_blackman_harris_window_moments():
+    """4-term Blackman-Harris (Harris 1978) sampled as H((j xi_s/L - xi_k)/Omega_k):
+    mean over the support a0 = 0.35875, mean square a0^2 + (a1^2 + a2^2 + a3^2)/2
+    (the cosines integrate to 0 over whole periods), peak 1 at the centre."""
+    a = (0.35875, 0.48829, 0.14128, 0.01168)
+    sys_ = O.nsg_system(BH)
+    L = sys_.L
+    checked = 0
+    for k in range(1, sys_.K + 1):
+        ch = sys_.channels[k]
+        Lk = sys_.Omega[k] * L / BH.fs
+        if Lk >= 200:
+            assert abs(ch.g.sum() / Lk - a[0]) < 2.0 / Lk
+            assert abs((ch.g ** 2).sum() / Lk - (a[0] ** 2 + (a[1] ** 2 + a[2] ** 2 + a[3] ** 2) / 2)) < 2.0 / Lk
+            assert abs(ch.g.max() - 1.0) < 1e-3
+            checked += 1
+    assert checked > 5
+
+
+@pytest.mark.parametrize("n", [30001, 8192])
+def test_blackman_harris_perfect_reconstruction(n):
+    """Prop. 3 holds for any admissible window: the canonical dual of the
+    Blackman-Harris system reconstructs (painless frame, eq. painlessframe1)."""
+    plan = O.make_plan(BH)
+    assert plan.dual is not None
+    f = _rng(n + 11).standard_normal(n)
+    fr = O.slicq_inverse(O.slicq_forward(f, plan), plan, n)
+    assert np.linalg.norm(fr - f) / np.linalg.norm(f) < 1e-12
+
+
+def test_blackman_harris_changes_only_the_window_values():
+    """Same supports J_k and band lengths as Hann (the support is |t| < 1/2 for
+    both), different values."""
+    h = O.make_plan(O.SliCQParams(44100.0, 50.0, 22050.0, 12, 8192, 2048))
+    b = O.make_plan(BH)
+    for ch, cb in zip(h.sys.channels, b.sys.channels):
+        assert (ch.j0, ch.length, ch.M) == (cb.j0, cb.length, cb.M)
+    k = h.K // 2
+    assert not np.allclose(h.sys.channels[k].g, b.sys.channels[k].g)
