@@ -61,7 +61,10 @@ typedef enum {
   SLICQ_EUNSUPPORTED = 6  /* valid parameters outside what this build runs */
 } slicq_status;
 
-typedef enum { SLICQ_WIN_HANN = 0 } slicq_window;          /* H of Sec. 3 */
+typedef enum {                                             /* H of Sec. 3 */
+  SLICQ_WIN_HANN = 0,             /* cos^2(pi t) on |t| < 1/2 */
+  SLICQ_WIN_BLACKMAN_HARRIS = 1   /* 4-term Blackman-Harris (Harris 1978), centred, |t| < 1/2 */
+} slicq_window;
 typedef enum {                                             /* M_k choice */
   SLICQ_MK_POW2 = 0,   /* M_k = max(16, next power of two >= |J_k|) */
   SLICQ_MK_MULT4 = 1,  /* smallest multiple of 4 >= |J_k|: not built (EUNSUPPORTED) */
@@ -79,7 +82,8 @@ typedef enum {                                             /* M_k choice */
  *   trans_len        M, the Tukey transition length, even, 2 <= M < N.
  *   min_filter_len   lower bound on the support of g_k in samples (Sec. 5.2;
  *                    16 is the paper's recommendation). >= 1.
- *   window           SLICQ_WIN_HANN.
+ *   window           SLICQ_WIN_HANN or SLICQ_WIN_BLACKMAN_HARRIS (same
+ *                    supports J_k, different values; plateaus stay flat).
  *   mk_policy        SLICQ_MK_POW2: M_k = max(16, next power of two >= |J_k|).
  *                    SLICQ_MK_CONST: every M_k is the largest of those, so
  *                    each slice's coefficients form a (K+2) x M array (the

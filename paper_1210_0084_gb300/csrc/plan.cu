@@ -39,7 +39,7 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
   if (!(p->fs > 0) || !(p->fmin > 0) || !(p->fmax > p->fmin) || p->bins_per_octave < 1 ||
       p->min_filter_len < 1 || !std::isfinite(p->fs) || !std::isfinite(p->fmax))
     return SLICQ_EINVAL;
-  if (p->window != SLICQ_WIN_HANN) return SLICQ_EINVAL;
+  if (p->window != SLICQ_WIN_HANN && p->window != SLICQ_WIN_BLACKMAN_HARRIS) return SLICQ_EINVAL;
   if (p->mk_policy == SLICQ_MK_MULT4) return SLICQ_EUNSUPPORTED;  // band FFTs are radix-2
   if (p->mk_policy != SLICQ_MK_POW2 && p->mk_policy != SLICQ_MK_CONST) return SLICQ_EINVAL;
   const int64_t L2 = p->slice_len;
@@ -362,16 +362,22 @@ struct WinJob {
   int32_t len, win_off, plateau, M, j0, pair;  // pair: channel has a mirror
 };
 
-__device__ double hann_or_plateau(const WinJob& w, int64_t j, double fs, double L2) {
+// H((j xi_s / 2N - xi_k) / Omega_k): Hann cos^2(pi t), or the 4-term
+// Blackman-Harris window of F. J. Harris (Proc. IEEE 66(1), 1978),
+// a0 - a1 cos 2 pi x + a2 cos 4 pi x - a3 cos 6 pi x on x in [0, 1], centred
+// (x = t + 1/2: the odd terms change sign); plateaus are flat.
+__device__ double window_value(const WinJob& w, int64_t j, double fs, double L2, int shape) {
   if (w.plateau) return 1.0;
   const double t = ((double)j * fs / L2 - w.xi) / w.omega;
   if (fabs(t) >= 0.5) return 0.0;
+  if (shape == SLICQ_WIN_BLACKMAN_HARRIS)
+    return 0.35875 + 0.48829 * cospi(2.0 * t) + 0.14128 * cospi(4.0 * t) + 0.01168 * cospi(6.0 * t);
   const double c = cospi(t);
   return c * c;
 }
 
 // g_k on its support, FP64
-__global__ void k_windows(const WinJob* jobs, int nch, int64_t total, double fs, double L2,
+__global__ void k_windows(const WinJob* jobs, int nch, int64_t total, double fs, double L2, int shape,
                           double* g64) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= total) return;
@@ -381,7 +387,7 @@ __global__ void k_windows(const WinJob* jobs, int nch, int64_t total, double fs,
     if (jobs[mid].win_off <= i) lo = mid; else hi = mid - 1;
   }
   const WinJob w = jobs[lo];
-  g64[i] = hann_or_plateau(w, w.jlo + (i - w.win_off), fs, L2);
+  g64[i] = window_value(w, w.jlo + (i - w.win_off), fs, L2, shape);
 }
 
 // d[j] = sum_k M_k (g_k[j]^2 + [k has a mirror] g_k[-j]^2) over the circle
@@ -718,7 +724,7 @@ slicq_status build_tables(slicq_plan* pl) {
     const int T = 256;
     if (e == cudaSuccess && pl->win_total > 0) {
       k_windows<<<(unsigned)((pl->win_total + T - 1) / T), T>>>(d_jobs, nch, pl->win_total, pl->params.fs,
-                                                                (double)L2, d_g64);
+                                                                (double)L2, pl->params.window, d_g64);
       e = cudaGetLastError();
     }
     if (e == cudaSuccess) {

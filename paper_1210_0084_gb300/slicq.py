@@ -119,12 +119,14 @@ class SliCQParams:
     min_filter_len: int = 16
     slice_cluster: int = 0
     mk_policy: str = "pow2"   # "pow2" or "const" (rectangular representation)
+    window: str = "hann"      # "hann" or "blackman_harris"
 
     def to_c(self) -> _Params:
         mk = {"pow2": 0, "mult4": 1, "const": 2}[self.mk_policy]
+        win = {"hann": 0, "blackman_harris": 1}[self.window]
         return _Params(float(self.fs), float(self.fmin), float(self.fmax),
                        int(self.bins_per_octave), int(self.min_filter_len),
-                       int(self.slice_len), int(self.trans_len), 0, mk,
+                       int(self.slice_len), int(self.trans_len), win, mk,
                        int(self.slice_cluster), 0)
 
 

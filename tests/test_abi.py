@@ -49,15 +49,17 @@ CASES = [
     S.SliCQParams(16000.0, 50.0, 8000.0, 24, 2048, 512),
     S.SliCQParams(16000.0, 50.0, 8000.0, 24, 2048, 512, mk_policy="const"),
     S.SliCQParams(44100.0, 32.7, 22050.0, 48, 65536, 16384, mk_policy="const"),
+    S.SliCQParams(44100.0, 50.0, 22050.0, 12, 8192, 2048, window="blackman_harris"),
 ]
 
 
 @pytest.mark.parametrize("p", CASES,
-                         ids=lambda p: f"fs{int(p.fs)}_B{p.bins_per_octave}_L{p.slice_len}_{p.mk_policy}")
+                         ids=lambda p: f"fs{int(p.fs)}_B{p.bins_per_octave}_L{p.slice_len}_{p.mk_policy}_{p.window}")
 def test_host_layout_matches_oracle(lib, p):
     lay = S.layout(p)
     op = O.make_plan(O.SliCQParams(p.fs, p.fmin, p.fmax, p.bins_per_octave, p.slice_len,
-                                   p.trans_len, p.min_filter_len, mk_policy=p.mk_policy))
+                                   p.trans_len, p.min_filter_len, mk_policy=p.mk_policy,
+                                   window=p.window))
     K = op.K
     assert lay["M"].shape[0] == K + 2
     chans = op.sys.channels[: K + 2]

@@ -35,7 +35,8 @@ def S():
 
 def _oplan(p):
     return O.make_plan(O.SliCQParams(p.fs, p.fmin, p.fmax, p.bins_per_octave, p.slice_len,
-                                     p.trans_len, p.min_filter_len, mk_policy=p.mk_policy))
+                                     p.trans_len, p.min_filter_len, mk_policy=p.mk_policy,
+                                     window=p.window))
 
 
 def _rel(a, b):
@@ -66,19 +67,22 @@ SMALL = [
     (44100.0, 50.0, 22050.0, 12, 4096, 1026, 20000, 2),    # transition = 2 mod 4, odd a0
     (16000.0, 50.0, 8000.0, 24, 2048, 512, 7000, 2, "const"),  # rectangular: one M_k
     (44100.0, 50.0, 22050.0, 12, 8192, 2048, 30000, 1, "const"),
+    (44100.0, 50.0, 22050.0, 12, 8192, 2048, 30000, 2, "pow2", "blackman_harris"),
+    (16000.0, 50.0, 8000.0, 24, 2048, 512, 7000, 1, "const", "blackman_harris"),
 ]
 
 
 def _params(S, c):
     fs, fmin, fmax, B, L2, M, n, batch = c[:8]
-    return S.SliCQParams(fs, fmin, fmax, B, L2, M, mk_policy=c[8] if len(c) > 8 else "pow2"), n, batch
+    return S.SliCQParams(fs, fmin, fmax, B, L2, M, mk_policy=c[8] if len(c) > 8 else "pow2",
+                         window=c[9] if len(c) > 9 else "hann"), n, batch
 
 
 def _signal(n, fs, batch, seed):
     return np.stack([signals.noise_plus_sines(n, fs, seed + i) for i in range(batch)])
 
 
-@pytest.mark.parametrize("case", SMALL, ids=lambda c: f"L{c[4]}_B{c[3]}_n{c[6]}x{c[7]}" + ("_const" if len(c) > 8 else ""))
+@pytest.mark.parametrize("case", SMALL, ids=lambda c: f"L{c[4]}_B{c[3]}_n{c[6]}x{c[7]}" + "".join("_" + x for x in c[8:]))
 def test_forward_inverse_adjoint_parity(S, case):
     p, n, batch = _params(S, case)
     plan = S.SliCQPlan(p)
@@ -110,8 +114,9 @@ def test_forward_inverse_adjoint_parity(S, case):
         assert np.abs(ya[b] - ra).max() <= ELEM * np.abs(ra).max()
 
 
-def test_plan_tables_match_oracle(S):
-    p = S.SliCQParams(44100.0, 32.7, 22050.0, 48, 65536, 16384)
+@pytest.mark.parametrize("window", ["hann", "blackman_harris"])
+def test_plan_tables_match_oracle(S, window):
+    p = S.SliCQParams(44100.0, 32.7, 22050.0, 48, 65536, 16384, window=window)
     plan = S.SliCQPlan(p)
     op = _oplan(p)
     K = op.K
