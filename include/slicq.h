@@ -246,6 +246,42 @@ SLICQ_API slicq_status slicq_batch_inverse(const slicq_batch* batch, const float
                                            cudaStream_t stream);
 
 /*
+ * Streaming sliCQ (real-time mode with bounded delay; the paper's framework
+ * is built for it, Sec. 4): one slice per call, N = slice_len / 2 samples
+ * per call in either direction (slicq_stream_hop).
+ *   slicq_stream_create   device state for one stream of `plan` (input and
+ *                         output rings of 2N samples, one slice's
+ *                         workspace); allocates; the plan must outlive it.
+ *   slicq_stream_forward  d_in: device, N new float samples (the block
+ *                         [mN, (m+1)N) of call m); d_coef: device, complex64
+ *                         [coefs_per_slice], 8-byte aligned, receives slice
+ *                         m, which covers [(m-1)N, (m+1)N) (Algorithm 3;
+ *                         samples before the first block are zero).  Equals
+ *                         slice m of slicq_forward of the whole signal when
+ *                         that signal ends with at least N zeros.
+ *   slicq_stream_inverse  d_coef: one slice's coefficients (call m: slice
+ *                         m); d_out: device, N floats, receives output
+ *                         samples (m-1)N + a0 + 1 .. mN + a0,
+ *                         a0 = (N - trans_len)/2 (Algorithm 4; the first
+ *                         call's samples before time 0 lack slice -1).
+ *   slicq_stream_reset    back to the start (zero history), asynchronous.
+ * A stream's calls are asynchronous on `stream` and must not overlap in time
+ * (each call's state is the previous call's result).  The forward and the
+ * inverse directions of one stream are independent.
+ * Errors: SLICQ_EINVAL (null pointers, misaligned d_coef), SLICQ_ENOMEM,
+ * SLICQ_ECUDA.
+ */
+typedef struct slicq_stream slicq_stream;
+SLICQ_API slicq_status slicq_stream_create(const slicq_plan* plan, slicq_stream** out);
+SLICQ_API void slicq_stream_destroy(slicq_stream* stream_state);
+SLICQ_API int64_t slicq_stream_hop(const slicq_plan* plan);
+SLICQ_API slicq_status slicq_stream_forward(slicq_stream* stream_state, const float* d_in, float* d_coef,
+                                            cudaStream_t stream);
+SLICQ_API slicq_status slicq_stream_inverse(slicq_stream* stream_state, const float* d_coef, float* d_out,
+                                            cudaStream_t stream);
+SLICQ_API slicq_status slicq_stream_reset(slicq_stream* stream_state, cudaStream_t stream);
+
+/*
  * sliCQ spectrogram (Sec. 4.1): |s^0 + s^1|^2, where the 2-layer array s^l
  * holds slice m's coefficient n of channel k in layer l = m mod 2 at time
  * index t = n + (m-1) M_k / 2 (circular in S M_k / 2), i.e. at time

@@ -28,7 +28,7 @@ import numpy as np
 
 __all__ = [
     "SliCQParams", "SliCQPlan", "SliCQError", "SliCQFunction", "slicq_transform",
-    "layout", "lib_path", "load_library", "STATUS", "SliCQBatch",
+    "layout", "lib_path", "load_library", "STATUS", "SliCQBatch", "SliCQStream",
 ]
 
 _PKG = os.path.dirname(os.path.abspath(__file__))
@@ -85,6 +85,12 @@ def load_library():
         "slicq_plan_table": (ctypes.c_int, [VP, I32, VP, I64, ctypes.POINTER(I64)]),
         "slicq_trace_enable": (ctypes.c_int, [VP, I32]),
         "slicq_spectrogram": (ctypes.c_int, [VP, VP, I64, I64, VP, I64, VP]),
+        "slicq_stream_create": (ctypes.c_int, [VP, ctypes.POINTER(VP)]),
+        "slicq_stream_destroy": (None, [VP]),
+        "slicq_stream_hop": (I64, [VP]),
+        "slicq_stream_forward": (ctypes.c_int, [VP, VP, VP, VP]),
+        "slicq_stream_inverse": (ctypes.c_int, [VP, VP, VP, VP]),
+        "slicq_stream_reset": (ctypes.c_int, [VP, VP]),
         "slicq_batch_create": (ctypes.c_int, [VP, I32, VP, VP, I32, ctypes.POINTER(VP)]),
         "slicq_batch_destroy": (None, [VP]),
         "slicq_batch_layout": (ctypes.c_int, [VP, VP, VP, VP, ctypes.POINTER(I64), ctypes.POINTER(I64),
@@ -344,6 +350,59 @@ def SliCQFunction():
 def slicq_transform(x, plan: SliCQPlan):
     """Differentiable forward sliCQ of a float32 CUDA tensor [batch, n]."""
     return SliCQFunction().apply(x, plan)
+
+
+class SliCQStream:
+    """Streaming sliCQ of one plan: N = slice_len / 2 samples per call.
+
+    ``forward(block)`` takes the next N samples (float32 CUDA) and returns
+    slice m (complex64 [coefs_per_slice]); ``inverse(c)`` takes one slice's
+    coefficients and returns the N output samples (m-1)N + a0 + 1 .. mN + a0.
+    """
+
+    def __init__(self, plan: SliCQPlan):
+        import torch
+        self._torch = torch
+        self.plan = plan
+        self.lib = plan.lib
+        h = ctypes.c_void_p()
+        _check(self.lib.slicq_stream_create(plan.handle, ctypes.byref(h)), "slicq_stream_create")
+        self._h = h
+        self.hop = int(self.lib.slicq_stream_hop(plan.handle))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            self.lib.slicq_stream_destroy(h)
+            self._h = None
+
+    def _stream(self):
+        return ctypes.c_void_p(self._torch.cuda.current_stream(self.plan.device).cuda_stream)
+
+    def forward(self, block, out=None):
+        t = self._torch
+        if block.dtype != t.float32 or not block.is_cuda or block.numel() != self.hop:
+            raise ValueError(f"expected {self.hop} float32 CUDA samples")
+        block = block.contiguous()
+        if out is None:
+            out = t.empty(self.plan.coefs_per_slice, dtype=t.complex64, device=block.device)
+        _check(self.lib.slicq_stream_forward(self._h, block.data_ptr(), out.data_ptr(), self._stream()),
+               "slicq_stream_forward")
+        return out
+
+    def inverse(self, coef, out=None):
+        t = self._torch
+        if coef.dtype != t.complex64 or not coef.is_cuda or coef.numel() != self.plan.coefs_per_slice:
+            raise ValueError("expected one slice of complex64 CUDA coefficients")
+        coef = coef.contiguous()
+        if out is None:
+            out = t.empty(self.hop, dtype=t.float32, device=coef.device)
+        _check(self.lib.slicq_stream_inverse(self._h, coef.data_ptr(), out.data_ptr(), self._stream()),
+               "slicq_stream_inverse")
+        return out
+
+    def reset(self):
+        _check(self.lib.slicq_stream_reset(self._h, self._stream()), "slicq_stream_reset")
 
 
 class SliCQBatch:
