@@ -448,6 +448,34 @@ def main():
                                  "frac": sp_bytes / (sp_avg * 1e-3) / 1e9 / peak,
                                  "bound": "hbm", "peak_kind": f"of {peak_kind}"}}
 
+    # streaming mode: one slice per call (N new samples in, one slice of
+    # coefficients out; one slice in, N samples out), per-call latency
+    from paper_1210_0084_gb300.slicq import SliCQStream
+    sst = SliCQStream(plan)
+    hop = sst.hop
+    blk = xd[0, :hop].contiguous()
+    cs = torch.empty(cps, dtype=torch.complex64, device=dev)
+    ys = torch.empty(hop, dtype=torch.float32, device=dev)
+    for _ in range(5):
+        sst.forward(blk, out=cs)
+        sst.inverse(cs, out=ys)
+    f_ms, i_ms = [], []
+    for _ in range(20):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        sst.forward(blk, out=cs)
+        e1.record(stream)
+        sst.inverse(cs, out=ys)
+        e2.record(stream)
+        torch.cuda.synchronize()
+        f_ms.append(e0.elapsed_time(e1))
+        i_ms.append(e1.elapsed_time(e2))
+    fm, im = statistics.median(f_ms), statistics.median(i_ms)
+    streaming = {"hop_samples": hop, "forward_ms_per_call": fm, "inverse_ms_per_call": im,
+                 "realtime_factor": (hop / WORKLOAD["fs"]) / ((fm + im) * 1e-3),
+                 "delay_samples": "one slice: output lags input by N - a0 - 1 after a slice's block"}
+    del sst
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(x)
@@ -459,6 +487,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": _config(world, args.mk_policy), "recon_rel_err": recon_err,
             "roofline": roofline, "step_roofline": step_roof, "kernels": kern, "epilogues": epilogues,
+            "streaming": streaming,
             "gpu_launches": len(traced), "e2e": e2e, "cpu_baseline": cpu,
             "clocks": sampler.summary(), "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms),
         }
