@@ -155,9 +155,10 @@ SLICQ_API int64_t slicq_num_slices(const slicq_plan* plan, int64_t n_samples);
 /*
  * Device workspace (bytes) that forward / inverse / adjoint need for
  * `batch` signals of n_samples.  The workspace holds slice spectra and the
- * small hand-off areas that make the overlap-adds deterministic.  It must be
- * zero-filled once after allocation; every completed call leaves it ready
- * for the next.  Calls that share a workspace must not overlap in time.
+ * partial sums (band bins several groups share, transition samples two
+ * slices share) that make the overlap-adds deterministic.  It needs no
+ * initialisation: every call writes each value before reading it.  Calls
+ * that share a workspace must not overlap in time.
  */
 SLICQ_API slicq_status slicq_workspace_size(const slicq_plan* plan, int64_t n_samples,
                                   int64_t batch, size_t* bytes);
@@ -225,7 +226,7 @@ SLICQ_API slicq_status slicq_plan_table(const slicq_plan* plan, int32_t which,
  *   coefficients  one interleaved complex buffer; clip c's slices
  *                 (h_slices[c] of them, its plan's coefs_per_slice each) at
  *                 h_coef_off[c] complex values; coef_total in all
- *   workspace     work_bytes, 256-byte aligned, zero-filled once
+ *   workspace     work_bytes, 256-byte aligned (no initialisation needed)
  */
 typedef struct slicq_batch slicq_batch;
 SLICQ_API slicq_status slicq_batch_create(const slicq_plan* const* plans, int32_t n_plans,

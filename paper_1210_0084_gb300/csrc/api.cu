@@ -73,14 +73,12 @@ size_t workspace_layout(const slicq_plan* pl, int64_t n, int64_t batch, void* ba
   const int64_t slices = batch * w.S;
   size_t off = 0;
   auto take = [&](size_t bytes) { const size_t o = off; off = align256(off + bytes); return o; };
-  const size_t o_items = take(2 * sizeof(unsigned long long));
   const size_t o_spec = take(sizeof(float2) * slices * w.spec_stride);
   const size_t o_bp = take(sizeof(float2) * slices * std::max(pl->ovl_total, 1));
   const size_t o_op = take(sizeof(float) * slices * 2 * ((pl->params.trans_len + 3) & ~int64_t(3)));
   w.bytes = off;
   if (base) {
     char* b = (char*)base;
-    w.items = (unsigned long long*)(b + o_items);
     w.spec = (float2*)(b + o_spec);
     w.band_patch = (float2*)(b + o_bp);
     w.ola_patch = (float*)(b + o_op);
@@ -96,14 +94,12 @@ size_t workspace_layout_rows(const slicq_plan* pl, int64_t rows, void* base, Wor
   w.spec_stride = pl->N + 2;
   size_t off = 0;
   auto take = [&](size_t bytes) { const size_t o = off; off = align256(off + bytes); return o; };
-  const size_t o_items = take(2 * sizeof(unsigned long long));
   const size_t o_spec = take(sizeof(float2) * rows * w.spec_stride);
   const size_t o_bp = take(sizeof(float2) * rows * std::max(pl->ovl_total, 1));
   const size_t o_op = take(sizeof(float) * rows * 2 * ((pl->params.trans_len + 3) & ~int64_t(3)));
   w.bytes = off;
   if (base) {
     char* b = (char*)base;
-    w.items = (unsigned long long*)(b + o_items);
     w.spec = (float2*)(b + o_spec);
     w.band_patch = (float2*)(b + o_bp);
     w.ola_patch = (float*)(b + o_op);

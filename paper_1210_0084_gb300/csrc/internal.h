@@ -99,10 +99,7 @@ struct slicq_plan {
   int C = 1;              // cluster size of the slice kernels
   int G = 0;              // band groups
   int ovl_total = 0;      // patch slots of one slice: sum over shared bins of their group count
-  int band_smem_a = 0;    // dynamic shared memory of band analysis (bytes)
   int band_smem_s = 0;    // dynamic shared memory of band synthesis (bytes)
-  int band_in_a = 0;      // complex values per staged analysis input (max footprint)
-  int band_in_s = 0;      // complex values per staged synthesis input (max group block)
   int num_sms = 152;      // SMs of the plan's device (grid sizing)
   int slots_a = 152;      // CTAs the persistent band analysis runs (SMs x CTAs per SM)
   int slots_s = 152;      // CTAs the persistent band synthesis runs
@@ -167,7 +164,6 @@ size_t workspace_layout_rows(const slicq_plan* pl, int64_t rows, void* base, str
 // Workspace partition for (n_samples, batch).
 struct Workspace {
   int64_t S = 0, L = 0;
-  unsigned long long* items = nullptr;  // [2] work counters of the band kernels
   int64_t spec_stride = 0;         // complex values per slice spectrum row
   float2* spec = nullptr;          // [batch * S][spec_stride]
   float2* band_patch = nullptr;    // [batch * S][ovl_total]: partial sums of shared bins

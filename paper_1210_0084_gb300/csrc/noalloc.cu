@@ -56,10 +56,9 @@ extern "C" slicq_status slicq_forward_noalloc(const slicq_plan* plan, const floa
   workspace_layout(plan, n_samples, batch, nullptr, &ws);
   if (ws.L >= (int64_t(1) << 31)) return SLICQ_EUNSUPPORTED;  // positions are 32-bit
   if (coef_capacity < batch * ws.S * plan->coefs_per_slice) return SLICQ_ESIZE;
-  // the array holds the band kernels' work counter (first 256 bytes, reset by
-  // the slice kernel of every call) and then the slice spectra
+  // the array holds the slice spectra
   const size_t spec_bytes = sizeof(float2) * (size_t)(batch * ws.S) * (size_t)ws.spec_stride;
-  if (spec_bytes > kNoAllocScratchBytes - 256) return SLICQ_ESIZE;  // beyond the fixed array
+  if (spec_bytes > kNoAllocScratchBytes) return SLICQ_ESIZE;  // beyond the fixed array
 
   int cur = 0;
   if (cudaGetDevice(&cur) != cudaSuccess) return SLICQ_ECUDA;
@@ -67,11 +66,9 @@ extern "C" slicq_status slicq_forward_noalloc(const slicq_plan* plan, const floa
   void* scratch = nullptr;
   cudaError_t e = noalloc_scratch(plan->device, &scratch);
   if (e == cudaSuccess) {
-    // only the spectra and the work counter are used: the forward kernels read
-    // nothing else of a workspace, every spectrum value is written before it
-    // is read, and the slice kernel resets the counter
-    ws.items = reinterpret_cast<unsigned long long*>(scratch);
-    ws.spec = reinterpret_cast<float2*>(reinterpret_cast<char*>(scratch) + 256);
+    // only the spectra are used: the forward kernels read nothing else of a
+    // workspace, and every spectrum value is written before it is read
+    ws.spec = reinterpret_cast<float2*>(scratch);
     e = launch_slice_forward(plan, d_f, n_samples, batch, ws, stream);
     if (e == cudaSuccess) e = launch_band_analysis(plan, ws, batch, reinterpret_cast<float2*>(d_coef), stream);
   }

@@ -162,7 +162,7 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
   // ---- band groups: consecutive channels, <= kBandThreads threads each
   pl->groups.clear();
   pl->thread_band.clear();
-  int in_a = 0, in_s = 0, tb_max = 0, smem_p = 0, syn_max = 0;  // complex values
+  int smem_p = 0, syn_max = 0;  // complex values
   pl->cost_a.clear();
   pl->cost_s.clear();
   {
@@ -243,9 +243,6 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
         const int nb = gd.band_end - gd.band_begin;
         const int bufl = gd.log2M > kMaxTwoPassLog2 ? M + 1
                                                     : M + (M >> ((gd.log2M + 1) / 2)) + 1;
-        in_a = std::max(in_a, gd.fp_len);
-        in_s = std::max(in_s, nb * M);
-        tb_max = std::max(tb_max, nb * bufl);
         // synthesis: [pass-2 twiddles (two-pass lengths)][team buffers][layers]
         const int lay = ((gd.nphases & 0xFFFF) + (gd.nphases >> 16)) * (gd.acc_hi - gd.acc_lo);
         syn_max = std::max(syn_max, (((gd.log2M > kMaxTwoPassLog2 ? 0 : M) + nb * bufl + 1) & ~1) + lay);
@@ -315,14 +312,11 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
     gd.ex_hi = g + 1 < G ? std::min(gd.acc_hi, pl->groups[g + 1].acc_lo) : gd.acc_hi;
     if (gd.ex_hi < gd.ex_lo) gd.ex_hi = gd.ex_lo;
   }
-  pl->band_in_a = (in_a + 1) & ~1;
-  pl->band_in_s = (in_s + 1) & ~1;
   // per-slice band kernels: one team buffer per channel of the group
-  pl->band_smem_a = tb_max * (int)sizeof(float2);
   pl->band_smem_s = syn_max * (int)sizeof(float2);
   pl->band_smem_p = smem_p * (int)sizeof(float2);
   if (pl->band_smem_p > 220 * 1024) return SLICQ_EUNSUPPORTED;
-  if (pl->band_smem_a > 220 * 1024 || pl->band_smem_s > 220 * 1024) return SLICQ_EUNSUPPORTED;
+  if (pl->band_smem_s > 220 * 1024) return SLICQ_EUNSUPPORTED;
 
   // ---- slice FFT geometry: N = P Q, cluster of C CTAs, <= 256 threads each
   const int logN = ilog2_64(N);

@@ -47,7 +47,6 @@ struct SliceArgs {
   int tw_off;                     // shared-memory offset (float2) of the table copy
   float* ola_patch;               // [slice][2][ola_stride]: the two sides of each transition
   int ola_stride;                 // Mtr rounded up to a multiple of 4
-  unsigned long long* items;      // band-kernel work counter this launch resets
   const RowDesc* __restrict__ rows;  // ragged batch: per-row clip description (or null)
   int adjoint;                    // multiply the output by h_0 instead of 1
 };
@@ -249,8 +248,6 @@ __global__ void __launch_bounds__(kSliceMaxThreads, 2) slice_forward_kernel(Slic
   const SliceTables tabs = stage_twiddles<LOGP, LOGQ>(a, sm);
   const SmemTwiddles& tws = tabs.tw;
   pdl_wait();  // the input (and the previous kernel's use of the workspace)
-  // the band analysis that follows in the same stream counts its work items from 0
-  if (blockIdx.x == 0 && threadIdx.x == 0) *a.items = 0ull;
   const int Pc = 1 << a.logPc;
   {
     float2 res[TQ::HELD];
@@ -323,9 +320,6 @@ __global__ void __launch_bounds__(kSliceMaxThreads, 2) slice_inverse_kernel(Slic
   const SliceTables tabs = stage_twiddles<LOGP, LOGQ>(a, sm);
   const SmemTwiddles& tws = tabs.tw;
   pdl_wait();  // the synthesised spectra
-  // the band synthesis of the next call counts its work items from 0 (it has
-  // finished for this call: it precedes this kernel in the stream)
-  if (blockIdx.x == 0 && threadIdx.x == 0) *a.items = 0ull;
   __syncthreads();
   // Z[k] = (H[k] + conj H[N-k]) + i e^{+2 pi i k / 2N} (H[k] - conj H[N-k])
   auto load = [&](int k) -> float2 {
@@ -499,7 +493,6 @@ cudaError_t launch_slice_forward(const slicq_plan* pl, const float* f, int64_t n
                                  const Workspace& ws, cudaStream_t st, const RowDesc* rows) {
   SliceArgs a = make_args(pl, ws, n);
   a.f = f;
-  a.items = ws.items + 0;
   a.rows = rows;
   return dispatch(true, pl, a, batch * ws.S, st);
 }
@@ -508,7 +501,6 @@ cudaError_t launch_slice_inverse(const slicq_plan* pl, int64_t n, int64_t batch,
                                  const Workspace& ws, float* out, cudaStream_t st, const RowDesc* rows) {
   SliceArgs a = make_args(pl, ws, n);
   a.out = out;
-  a.items = ws.items + 1;
   a.rows = rows;
   a.adjoint = kind == kSynthAdjoint;
   return dispatch(false, pl, a, batch * ws.S, st);

@@ -199,7 +199,7 @@ class SliCQPlan:
         return sz.value
 
     def workspace(self, n: int, batch: int):
-        """Zero-filled device workspace for (n, batch), cached on the plan."""
+        """Device workspace for (n, batch), cached on the plan."""
         key = (int(n), int(batch))
         w = self._work.get(key)
         if w is None:
