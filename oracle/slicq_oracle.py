@@ -68,7 +68,7 @@ __all__ = [
     "nsgt_analysis", "nsgt_synthesis", "slicq_slices", "slicq_forward",
     "slicq_inverse", "slicq_adjoint", "slicq_forward_complex",
     "slicq_inverse_complex", "atoms", "frame_operator_matrix",
-    "num_slices", "padded_length", "two_layer_view", "slicq_spectrogram",
+    "num_slices", "padded_length", "two_layer_view", "slicq_spectrogram", "slicq_modify",
 ]
 
 # ---------------------------------------------------------------------------
@@ -601,3 +601,40 @@ def slicq_spectrogram(coef: np.ndarray, plan: SliCQPlan) -> np.ndarray:
     S off_k / 2)."""
     return np.concatenate([np.abs(two_layer_view(coef, plan, k).sum(axis=0)) ** 2
                            for k in range(plan.real_channels)])
+
+
+def slicq_modify(coef: np.ndarray, plan: SliCQPlan, shift: int = 0,
+                 mask: Optional[np.ndarray] = None) -> np.ndarray:
+    """Coefficients for transposition and masking in the rectangular
+    representation (Sec. 6: a translation of the spectrum along the channels,
+    8 channels = 2 semitones at B = 48).  The paper's coefficients of a
+    channel are at baseband; ours keep the channel's absolute frequency
+    (reading R13), so channel k = 1..K takes channel k - shift modulated by
+    the centre-bin difference: at global time t = (m-1)N + n a of slice m,
+    c'_k = c_{k-shift} exp(2 pi i (jc_k - jc_{k-shift}) t / 2N) with
+    jc_k = round(xi_k 2N / xi_s); zero when k - shift is outside 1..K.  The
+    plateaus k = 0, K+1 keep their own.  Then every coefficient is
+    multiplied by mask (same shape).  A shift needs one band length for all
+    channels (one time grid)."""
+    c = np.array(coef, dtype=np.complex128, copy=True)
+    if shift:
+        M = set(int(m) for m in plan.M[: plan.real_channels])
+        if len(M) != 1:
+            raise ValueError("a channel shift needs the rectangular representation")
+        (Mc,) = M
+        K, N = plan.K, plan.N
+        S = c.shape[0]
+        jc = np.rint(plan.sys.xi[: K + 2] * 2 * N / plan.params.fs).astype(np.int64)
+        t = (np.arange(S)[:, None] - 1) * N + np.arange(Mc)[None, :] * (2 * N // Mc)
+        out = c.copy()
+        for k in range(1, K + 1):
+            src = k - shift
+            if 1 <= src <= K:
+                dj = int(jc[k] - jc[src])
+                out[:, k * Mc:(k + 1) * Mc] = c[:, src * Mc:(src + 1) * Mc] * np.exp(2j * np.pi * dj * t / (2 * N))
+            else:
+                out[:, k * Mc:(k + 1) * Mc] = 0.0
+        c = out
+    if mask is not None:
+        c = c * mask
+    return c

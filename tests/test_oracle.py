@@ -478,3 +478,45 @@ def test_blackman_harris_changes_only_the_window_values():
         assert (ch.j0, ch.length, ch.M) == (cb.j0, cb.length, cb.M)
     k = h.K // 2
     assert not np.allclose(h.sys.channels[k].g, b.sys.channels[k].g)
+
+
+# ------------------------------------------- transposition and masking ---
+
+RECT = O.SliCQParams(44100.0, 50.0, 22050.0, 48, 8192, 2048, mk_policy="const")
+
+
+def _channel_energy(c, plan):
+    M = int(plan.M[0])
+    return np.array([np.sum(np.abs(c[2:-2, k * M:(k + 1) * M]) ** 2) for k in range(plan.real_channels)])
+
+
+@pytest.mark.parametrize("shift", [8, -8, 4])
+def test_transposition_moves_a_tone_by_the_shift(shift):
+    """Sec. 6: in the rectangular representation a shift by s channels
+    transposes by s/B octaves (8 channels = 2 semitones at B = 48): a tone
+    at xi_k0, shifted, resynthesised and analysed again, peaks in k0 + s."""
+    plan = O.make_plan(RECT)
+    n = 65536
+    t = np.arange(n) / RECT.fs
+    k0 = 200
+    f = np.sin(2 * np.pi * plan.sys.xi[k0] * t + 0.4)
+    g = O.slicq_inverse(O.slicq_modify(O.slicq_forward(f, plan), plan, shift=shift), plan, n)
+    assert int(np.argmax(_channel_energy(O.slicq_forward(g, plan), plan))) == k0 + shift
+
+
+def test_mask_selects_channels():
+    """A 0/1 mask over channels is a band-pass: the resynthesised signal has
+    no energy in the masked-out channels beyond the frame's overlap, and a
+    mask of ones is the identity (Prop. 3)."""
+    plan = O.make_plan(RECT)
+    n = 32768
+    f = _rng(3).standard_normal(n)
+    c = O.slicq_forward(f, plan)
+    ones = np.ones(c.shape)
+    assert np.linalg.norm(O.slicq_inverse(O.slicq_modify(c, plan, mask=ones), plan, n) - f) <= 1e-12 * np.linalg.norm(f)
+    M = int(plan.M[0])
+    mask = np.zeros(c.shape)
+    mask[:, 150 * M:200 * M] = 1.0
+    e = _channel_energy(O.slicq_forward(O.slicq_inverse(O.slicq_modify(c, plan, mask=mask), plan, n), plan), plan)
+    assert e[160:190].min() > 1e3 * e[:100].max()
+    assert e[160:190].min() > 1e3 * e[260:].max()
