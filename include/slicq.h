@@ -247,6 +247,28 @@ SLICQ_API slicq_status slicq_batch_inverse(const slicq_batch* batch, const float
                                            cudaStream_t stream);
 
 /*
+ * slicq_inverse with modified coefficients, for transposition and masking
+ * (Sec. 6; the modification is applied as the synthesis reads them):
+ *   channel_shift  s: channel k = 1..K is synthesised from channel k - s
+ *                  (zero where k - s is outside 1..K), modulated by the
+ *                  centre-bin difference exp(2 pi i (jc_k - jc_{k-s}) t / 2N),
+ *                  jc_k = round(xi_k 2N / xi_s), t = (m-1)N + n 2N/M the
+ *                  time of coefficient n of slice m (the coefficients of a
+ *                  channel keep its absolute frequency, so a translation
+ *                  along the channels needs this modulation).  s = 8 at
+ *                  B = 48 transposes by 2 semitones.  The plateau channels
+ *                  0 and K+1 keep their own.  s != 0 needs SLICQ_MK_CONST
+ *                  (one time grid for all channels), SLICQ_EINVAL otherwise.
+ *   d_mask         null, or device float [batch][S][coefs_per_slice]: gains
+ *                  multiplying the (shifted) coefficients; 4-byte aligned.
+ * Other arguments, layouts and errors as slicq_inverse.
+ */
+SLICQ_API slicq_status slicq_inverse_modified(const slicq_plan* plan, const float* d_coef,
+                                              int64_t n_samples, int64_t batch, int32_t channel_shift,
+                                              const float* d_mask, float* d_out, void* d_work,
+                                              size_t work_bytes, cudaStream_t stream);
+
+/*
  * Streaming sliCQ (real-time mode with bounded delay; the paper's framework
  * is built for it, Sec. 4): one slice per call, N = slice_len / 2 samples
  * per call in either direction (slicq_stream_hop).

@@ -229,14 +229,15 @@ slicq_status slicq_forward(const slicq_plan* plan, const float* d_f, int64_t n_s
 
 static slicq_status synthesis(const slicq_plan* plan, const float* d_coef, int64_t n_samples, int64_t batch,
                               float* d_out, void* d_work, size_t work_bytes, cudaStream_t stream,
-                              SynthKind kind) {
+                              SynthKind kind, const SynthModify* mod = nullptr) {
   Workspace ws;
   slicq_status st = check_common(plan, n_samples, batch, d_coef, d_out, d_work, work_bytes, &ws);
   if (st != SLICQ_OK) return st;
   if ((reinterpret_cast<uintptr_t>(d_coef) & 7) != 0) return SLICQ_EINVAL;
   return on_device(plan, [&] {
     cudaError_t e = traced(plan, 2, stream, [&] {
-      return launch_band_synthesis(plan, reinterpret_cast<const float2*>(d_coef), batch, kind, ws, stream); });
+      return launch_band_synthesis(plan, reinterpret_cast<const float2*>(d_coef), batch, kind, ws, stream,
+                                   nullptr, mod); });
     if (e == cudaSuccess && !plan->shared.empty())
       e = traced(plan, 4, stream, [&] { return launch_band_boundaries(plan, batch, ws, stream); });
     if (e == cudaSuccess)
@@ -256,6 +257,16 @@ slicq_status slicq_inverse(const slicq_plan* plan, const float* d_coef, int64_t 
 slicq_status slicq_adjoint(const slicq_plan* plan, const float* d_coef, int64_t n_samples, int64_t batch,
                            float* d_out, void* d_work, size_t work_bytes, cudaStream_t stream) {
   return synthesis(plan, d_coef, n_samples, batch, d_out, d_work, work_bytes, stream, kSynthAdjoint);
+}
+
+slicq_status slicq_inverse_modified(const slicq_plan* plan, const float* d_coef, int64_t n_samples,
+                                    int64_t batch, int32_t channel_shift, const float* d_mask, float* d_out,
+                                    void* d_work, size_t work_bytes, cudaStream_t stream) {
+  if (!plan) return SLICQ_EINVAL;
+  if (channel_shift != 0 && plan->params.mk_policy != SLICQ_MK_CONST) return SLICQ_EINVAL;
+  if ((reinterpret_cast<uintptr_t>(d_mask) & 3) != 0) return SLICQ_EINVAL;
+  const SynthModify mod{channel_shift, d_mask};
+  return synthesis(plan, d_coef, n_samples, batch, d_out, d_work, work_bytes, stream, kSynthInverse, &mod);
 }
 
 slicq_status slicq_spectrogram(const slicq_plan* plan, const float* d_coef, int64_t n_samples, int64_t batch,

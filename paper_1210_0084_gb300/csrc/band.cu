@@ -49,6 +49,13 @@ struct BandArgs {
   int ovl_total;
   int N;
   long long* cycles;                 // optional: SM clocks of each CTA (plan calibration)
+  // transposition and masking (synthesis only; see slicq_inverse_modified)
+  int modify;                        // 0: plain synthesis
+  int shift;                         // channel k = 1..K reads channel k - shift
+  int K;
+  int S_clip;                        // slices per clip (slice index m = row mod S_clip)
+  const int32_t* __restrict__ jc;    // centre bin of each channel, round(xi_k 2N / xi_s)
+  const float* __restrict__ mask;    // [row][cps] gains, or null
 };
 
 // --------------------------------------------------------------- cp.async ---
@@ -353,6 +360,38 @@ struct ChannelLayers {
   }
 };
 
+// Transposition: channel k = 1..K takes channel k - shift (none: src < 0)
+// modulated by the centre-bin difference dj (the coefficients keep their
+// absolute frequency); the plateaus k = 0, K+1 keep their own.
+struct ModSource {
+  int src;  // coefficient offset of the source channel in a slice, -1: zeros
+  int dj;
+};
+
+__device__ __forceinline__ ModSource mod_source(const BandArgs& a, int k, int own_off) {
+  if (!a.modify || a.shift == 0 || k == 0 || k == a.K + 1) return ModSource{own_off, 0};
+  const int src = k - a.shift;
+  if (src < 1 || src > a.K) return ModSource{-1, 0};
+  return ModSource{a.bands[src].coef_off, a.jc[k] - a.jc[src]};
+}
+
+// coefficient idx of channel k (offset own_off) in slice row s, modified:
+// times exp(2 pi i dj t / 2N) at t = (m-1)N + idx 2N/M, i.e.
+// (-1)^(dj (m-1)) exp(2 pi i (dj idx mod M) / M), then times the mask
+__device__ __forceinline__ float2 mod_value(const BandArgs& a, const ModSource& ms, int M, int own_off,
+                                            int64_t s, int idx, float2 v) {
+  if (ms.dj != 0) {
+    const int64_t m = s % a.S_clip;
+    const int e = (int)((((int64_t)ms.dj % M + M) % M * idx) & (M - 1));
+    float sn, cs;
+    sincospif(2.0f * (float)e / (float)M, &sn, &cs);
+    if ((ms.dj & 1) && ((m - 1) & 1)) { cs = -cs; sn = -sn; }
+    v = c_mul(v, make_float2(cs, sn));
+  }
+  if (a.mask) v = c_scale(v, __ldg(a.mask + s * a.cps + own_off + idx));
+  return v;
+}
+
 template <int LOGM>
 __device__ void synthesis_two_pass(const BandArgs& a, const GroupDesc& gd, int gi, int k, int lane, int lanes,
                                    int64_t total, float2* sm) {
@@ -401,9 +440,17 @@ __device__ void synthesis_two_pass(const BandArgs& a, const GroupDesc& gd, int g
   };
   // slice s's coefficients into the team buffer at their natural positions;
   // each thread copies exactly the elements it reads in pass 1
+  const ModSource ms = mod_source(a, k, bd.coef_off);
   auto fetch = [&](const Opaque& q, int64_t s) {
-    const float2* c = a.coef + s * a.cps + bd.coef_off;
     float2* buf = sm + q.buf;
+    if (ms.src < 0) {  // transposed from outside 1..K: zeros
+#pragma unroll
+      for (int i = 0; i < T::J1; ++i)
+#pragma unroll
+        for (int r = 0; r < T::R1; ++r) buf[q.tt + T::TT * i + r * T::R2] = make_float2(0.f, 0.f);
+      return;
+    }
+    const float2* c = a.coef + s * a.cps + ms.src;
 #pragma unroll
     for (int i = 0; i < T::J1; ++i)
 #pragma unroll
@@ -428,6 +475,13 @@ __device__ void synthesis_two_pass(const BandArgs& a, const GroupDesc& gd, int g
       for (int i = 0; i < T::J1; ++i)
 #pragma unroll
         for (int r = 0; r < T::R1; ++r) v[i][r] = buf[q.tt + T::TT * i + r * T::R2];
+      if (a.modify) {
+#pragma unroll
+        for (int i = 0; i < T::J1; ++i)
+#pragma unroll
+          for (int r = 0; r < T::R1; ++r)
+            v[i][r] = mod_value(a, ms, M, bd.coef_off, s, q.tt + T::TT * i + r * T::R2, v[i][r]);
+      }
     }
     __syncwarp();  // the team has read its inputs: pass 1 overwrites them
     if (active) team_pass1_regs<LOGM, -1>(q.tt, buf, v);
@@ -492,9 +546,14 @@ __device__ void synthesis_three_pass(const BandArgs& a, const GroupDesc& gd, int
   const float* __restrict__ gw = a.win + bd.win_off;
   zero_layers(lay, nl * acc_n);  // the transform's first barrier orders this
   pdl_wait();
+  const ModSource ms = mod_source(a, k, bd.coef_off);
   for (int64_t s = lane; s < total; s += lanes) {
-    const float2* c = a.coef + s * a.cps + bd.coef_off;
-    auto in = [&](int idx) { return __ldcs(c + idx); };
+    const float2* c = a.coef + s * a.cps + ms.src;
+    auto in = [&](int idx) {
+      if (!a.modify) return __ldcs(c + idx);
+      const float2 v = ms.src < 0 ? make_float2(0.f, 0.f) : __ldcs(c + idx);
+      return mod_value(a, ms, M, bd.coef_off, s, idx, v);
+    };
     auto contrib = [&](int idx, float2 v) {
       const int o = (idx - bd.j0) & (M - 1);
       if (o < bd.len) buf[o] = c_scale(v, __ldg(gw + o));
@@ -614,10 +673,18 @@ cudaError_t launch_band_analysis(const slicq_plan* pl, const Workspace& ws, int6
 
 cudaError_t launch_band_synthesis(const slicq_plan* pl, const float2* coef, int64_t batch,
                                   SynthKind kind, const Workspace& ws, cudaStream_t st,
-                                  long long* cycles) {
+                                  long long* cycles, const SynthModify* mod) {
   BandArgs a = make_args(pl, ws, kind == kSynthInverse ? pl->d_gs : pl->d_gadj);
   a.coef = const_cast<float2*>(coef);
   a.cycles = cycles;
+  if (mod && (mod->shift != 0 || mod->mask)) {
+    a.modify = 1;
+    a.shift = mod->shift;
+    a.mask = mod->mask;
+    a.K = pl->K;
+    a.S_clip = (int)ws.S;
+    a.jc = pl->d_jc;
+  }
   a.total = batch * ws.S;
   cudaError_t e = cudaFuncSetAttribute(band_synthesis_persistent_kernel,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, pl->band_smem_s);

@@ -127,6 +127,7 @@ struct slicq_plan {
   int32_t* d_slot_base = nullptr;  // slot_base on the device
   int4* d_shared = nullptr;        // shared on the device
   int2* d_half_chan = nullptr;     // [coefs_per_slice / 2]: (off_k, log2 M_k) of each half-coefficient
+  int32_t* d_jc = nullptr;         // [K+2] centre bin round(xi_k 2N / xi_s) (transposition)
   int16_t* d_thread_band = nullptr;
   float* d_ga = nullptr;    // g_k / sqrt(2N)
   float* d_gs = nullptr;    // w_k g~_k / sqrt(2N)
@@ -177,6 +178,13 @@ size_t workspace_layout(const slicq_plan* pl, int64_t n_samples, int64_t batch,
 cudaError_t launch_slice_forward(const slicq_plan* pl, const float* f,
                                  int64_t n, int64_t batch, const Workspace& ws,
                                  cudaStream_t st, const RowDesc* rows = nullptr);
+// Transposition and masking applied to the coefficients a synthesis reads
+// (slicq_inverse_modified).
+struct SynthModify {
+  int shift;          // channel k = 1..K reads channel k - shift
+  const float* mask;  // [batch * S][coefs_per_slice] gains, or null
+};
+
 // `cycles` (optional, one per CTA): SM clocks each CTA of the persistent
 // band kernel took, for the plan's lane calibration.
 cudaError_t launch_band_analysis(const slicq_plan* pl, const Workspace& ws,
@@ -185,7 +193,8 @@ cudaError_t launch_band_analysis(const slicq_plan* pl, const Workspace& ws,
 cudaError_t launch_band_synthesis(const slicq_plan* pl, const float2* coef,
                                   int64_t batch, SynthKind kind,
                                   const Workspace& ws, cudaStream_t st,
-                                  long long* cycles = nullptr);
+                                  long long* cycles = nullptr,
+                                  const SynthModify* mod = nullptr);
 // CTAs of the persistent band analysis (synthesis) one SM holds at the
 // plan's shared-memory sizes.
 int band_ctas_per_sm(const slicq_plan* pl, bool synthesis);

@@ -612,6 +612,10 @@ slicq_status build_tables(slicq_plan* pl) {
     for (int r = 0; r < (1 << (b.log2M - 1)); ++r) half[b.coef_off / 2 + r] = make_int2(b.coef_off, b.log2M);
   }
   const size_t o_half = take(sizeof(int2) * std::max<size_t>(half.size(), 1));
+  // transposition: centre bin of each channel (rounded to even on ties)
+  std::vector<int32_t> jc(nch);
+  for (int k = 0; k < nch; ++k) jc[k] = (int32_t)std::nearbyint(pl->xi[k] * (double)L2 / pl->params.fs);
+  const size_t o_jc = take(sizeof(int32_t) * nch);
   const size_t o_ga = take(sizeof(float) * (pl->win_total + 32));  // + padding
   const size_t o_gs = take(sizeof(float) * (pl->win_total + 32));  // + padding
   const size_t o_gadj = take(sizeof(float) * (pl->win_total + 32));  // + padding
@@ -652,6 +656,7 @@ slicq_status build_tables(slicq_plan* pl) {
   pl->d_slot_base = (int32_t*)(base + o_slot);
   pl->d_shared = (int4*)(base + o_shared);
   pl->d_half_chan = (int2*)(base + o_half);
+  pl->d_jc = (int32_t*)(base + o_jc);
   pl->d_ga = (float*)(base + o_ga);
   pl->d_gs = (float*)(base + o_gs);
   pl->d_gadj = (float*)(base + o_gadj);
@@ -685,6 +690,7 @@ slicq_status build_tables(slicq_plan* pl) {
                    cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !pl->shared.empty())
     e = cudaMemcpy(pl->d_shared, pl->shared.data(), sizeof(int4) * pl->shared.size(), cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(pl->d_jc, jc.data(), sizeof(int32_t) * nch, cudaMemcpyHostToDevice);
   if (e == cudaSuccess && !half.empty())
     e = cudaMemcpy(pl->d_half_chan, half.data(), sizeof(int2) * half.size(), cudaMemcpyHostToDevice);
   if (e == cudaSuccess)

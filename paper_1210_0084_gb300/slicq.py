@@ -85,6 +85,7 @@ def load_library():
         "slicq_plan_table": (ctypes.c_int, [VP, I32, VP, I64, ctypes.POINTER(I64)]),
         "slicq_trace_enable": (ctypes.c_int, [VP, I32]),
         "slicq_spectrogram": (ctypes.c_int, [VP, VP, I64, I64, VP, I64, VP]),
+        "slicq_inverse_modified": (ctypes.c_int, [VP, VP, I64, I64, I32, VP, VP, VP, SZ, VP]),
         "slicq_stream_create": (ctypes.c_int, [VP, ctypes.POINTER(VP)]),
         "slicq_stream_destroy": (None, [VP]),
         "slicq_stream_hop": (I64, [VP]),
@@ -286,6 +287,28 @@ class SliCQPlan:
     def adjoint(self, c, n: int, out=None):
         """Re(A^H c) [batch, n]: the gradient of the analysis map."""
         return self._synth(self.lib.slicq_adjoint, c, n, out, "slicq_adjoint")
+
+    def inverse_modified(self, c, n: int, shift: int = 0, mask=None, out=None):
+        """Real signal from modified coefficients (Sec. 6): channel k takes
+        channel k - shift, modulated to its own centre frequency, then times
+        ``mask`` (float32, same shape as ``c``); see slicq_inverse_modified."""
+        t = self._torch
+        squeeze = c.dim() == 2
+        c3 = (c.unsqueeze(0) if squeeze else c).contiguous()
+        batch = c3.shape[0]
+        mptr = None
+        if mask is not None:
+            m3 = (mask.unsqueeze(0) if mask.dim() == 2 else mask).contiguous()
+            if m3.dtype != t.float32 or tuple(m3.shape) != tuple(c3.shape):
+                raise ValueError("mask must be float32 with the coefficients' shape")
+            mptr = m3.data_ptr()
+        if out is None:
+            out = t.empty((batch, n), dtype=t.float32, device=c3.device)
+        w = self.workspace(n, batch)
+        _check(self.lib.slicq_inverse_modified(self._h, c3.data_ptr(), int(n), batch, int(shift), mptr,
+                                               out.data_ptr(), w.data_ptr(), w.numel(), self._stream()),
+               "slicq_inverse_modified")
+        return out[0] if squeeze else out
 
     def spectrogram(self, c, n: int, out=None):
         """sliCQ spectrogram |s^0 + s^1|^2 (Sec. 4.1), float32

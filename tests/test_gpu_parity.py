@@ -248,3 +248,38 @@ def test_spectrogram_parity(S, case):
     blocks = plan.spectrogram_blocks(spec, n)
     Sn = plan.num_slices(n)
     assert [int(bl.shape[-1]) for bl in blocks] == [Sn * int(m) // 2 for m in op.M[: op.real_channels]]
+
+
+@pytest.mark.parametrize("shift,masked,case", [
+    (8, False, (16000.0, 50.0, 8000.0, 24, 2048, 512, 7000, 2, "const")),
+    (-3, True, (16000.0, 50.0, 8000.0, 24, 2048, 512, 7000, 2, "const")),
+    (8, True, (44100.0, 50.0, 22050.0, 48, 8192, 2048, 30000, 1, "const")),
+    (0, True, SMALL[1]),
+])
+def test_inverse_modified_parity(S, shift, masked, case):
+    """Transposition and masking (Sec. 6) applied as the synthesis reads the
+    coefficients, against the oracle's inverse of the oracle-modified
+    coefficients (random gains; a shift only with one band length)."""
+    p, n, batch = _params(S, case)
+    plan = S.SliCQPlan(p)
+    op = _oplan(p)
+    x = _signal(n, p.fs, batch, 77)
+    c = plan.forward(torch.from_numpy(x).cuda())
+    mask = None
+    if masked:
+        mask = torch.from_numpy(np.random.default_rng(9).uniform(0.0, 2.0, size=c.shape).astype(np.float32)).cuda()
+    y = plan.inverse_modified(c, n, shift=shift, mask=mask).cpu().numpy()
+    cg = c.cpu().numpy().astype(np.complex128)
+    for b in range(batch):
+        mb = None if mask is None else mask[b].cpu().numpy().astype(np.float64)
+        ref = O.slicq_inverse(O.slicq_modify(cg[b], op, shift=shift, mask=mb), op, n)
+        assert _rel(y[b], ref) <= REL, _rel(y[b], ref)
+        assert np.abs(y[b] - ref).max() <= ELEM * np.abs(ref).max()
+
+
+def test_inverse_modified_shift_needs_rectangular(S):
+    p = S.SliCQParams(16000.0, 50.0, 8000.0, 24, 2048, 512)
+    plan = S.SliCQPlan(p)
+    c = plan.forward(torch.zeros(4096, device="cuda"))
+    with pytest.raises(S.SliCQError):
+        plan.inverse_modified(c, 4096, shift=2)
