@@ -45,6 +45,12 @@ R11 Windows live on the frequency circle: the sample j (any integer) has
 R12 Real signals keep channels 0..K+1; the dropped channels are the complex
     conjugates of the kept ones, and synthesis restores them before
     inverting (real part of the full synthesis).
+R13 Typos read as meant: the slicing line of Algorithm 3 is
+    f[j + (m-1)N] h_0[j - N], and the CQ-NSGT there acts on f^m.
+R14 Transposition (Sec. 6) translates baseband coefficients along the
+    channels; ours keep the channel's absolute frequency (R1 folds by the
+    absolute bin), so a shift by s channels also modulates by the centre-bin
+    difference (slicq_modify).
 
 Parity status: every public function is pinned by a test under ``tests/``
 (brute-force atoms, explicit frame operator, perfect reconstruction, tight
@@ -609,7 +615,7 @@ def slicq_modify(coef: np.ndarray, plan: SliCQPlan, shift: int = 0,
     representation (Sec. 6: a translation of the spectrum along the channels,
     8 channels = 2 semitones at B = 48).  The paper's coefficients of a
     channel are at baseband; ours keep the channel's absolute frequency
-    (reading R13), so channel k = 1..K takes channel k - shift modulated by
+    (readings R1, R14), so channel k = 1..K takes channel k - shift modulated by
     the centre-bin difference: at global time t = (m-1)N + n a of slice m,
     c'_k = c_{k-shift} exp(2 pi i (jc_k - jc_{k-shift}) t / 2N) with
     jc_k = round(xi_k 2N / xi_s); zero when k - shift is outside 1..K.  The
