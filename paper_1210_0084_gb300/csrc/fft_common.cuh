@@ -134,17 +134,17 @@ __device__ __forceinline__ void dft_reg(float2 (&v)[R]) {
 
 // ------------------------------------------- two-pass Stockham (team) ---
 // A DFT of length Lf = R1 * R2 (R1 = 2^ceil(log/2), R2 = 2^floor(log/2))
-// done by a team of TT = max(1, Lf/32) threads holding 32 (or Lf) values
-// each.  Pass 1: for j < R2, DFT_R1 over in[j + r R2], written to
+// done by a team of TT = max(1, Lf/PER) threads holding PER (or Lf) values
+// each (PER = 32, or 16 where R1, R2 <= 16).  Pass 1: for j < R2, DFT_R1 over in[j + r R2], written to
 // tmp[j R1 + r].  Pass 2: for j < R1, twiddle tmp[j + r R1] by
 // W_Lf^{j r}, DFT_R2, result is element j + r R1.  The shared buffer pads one
 // value per R1 (index x -> x + x / R1) so both passes are bank-conflict free.
-template <int LOGL>
+template <int LOGL, int PER = 32>
 struct Team {
   static constexpr int L = 1 << LOGL;
   static constexpr int R1 = 1 << ((LOGL + 1) / 2);
   static constexpr int R2 = L / R1;
-  static constexpr int TT = L >= 32 ? L / 32 : 1;
+  static constexpr int TT = L >= PER ? L / PER : 1;
   static constexpr int J1 = R2 / TT;    // pass-1 sub-transforms per thread
   static constexpr int J2 = R1 / TT;    // pass-2 sub-transforms per thread
   static constexpr int HELD = J2 * R2;  // values held after pass 2
@@ -155,10 +155,10 @@ struct Team {
 
 // Pass 1 on values already in registers: v[i][r] is input element
 // tt + TT i + r R2 (overwritten by the transform).
-template <int LOGL, int SIGN>
+template <int LOGL, int SIGN, int PER = 32>
 __device__ __forceinline__ void team_pass1_regs(int tt, float2* __restrict__ buf,
-                                                float2 (&v)[Team<LOGL>::J1][Team<LOGL>::R1]) {
-  using T = Team<LOGL>;
+                                                float2 (&v)[Team<LOGL, PER>::J1][Team<LOGL, PER>::R1]) {
+  using T = Team<LOGL, PER>;
 #pragma unroll
   for (int i = 0; i < T::J1; ++i) {
     const int j = tt + T::TT * i;
@@ -171,23 +171,23 @@ __device__ __forceinline__ void team_pass1_regs(int tt, float2* __restrict__ buf
 // Pass 1: LOAD(idx) gives input element idx (0 <= idx < L).  All of the
 // thread's loads are issued before the first DFT so that they are in flight
 // together.
-template <int LOGL, int SIGN, class Load>
+template <int LOGL, int SIGN, int PER = 32, class Load>
 __device__ __forceinline__ void team_pass1(int tt, float2* __restrict__ buf, Load load) {
-  using T = Team<LOGL>;
+  using T = Team<LOGL, PER>;
   float2 v[T::J1][T::R1];
 #pragma unroll
   for (int i = 0; i < T::J1; ++i)
 #pragma unroll
     for (int r = 0; r < T::R1; ++r) v[i][r] = load(tt + T::TT * i + r * T::R2);
-  team_pass1_regs<LOGL, SIGN>(tt, buf, v);
+  team_pass1_regs<LOGL, SIGN, PER>(tt, buf, v);
 }
 
 // Pass 2 (read half): twiddled, transformed values into res[i * R2 + r] for
 // element (tt + TT i) + r R1.  TW(j, r) returns exp(SIGN 2 pi i j r / Lf).
-template <int LOGL, int SIGN, class Tw>
+template <int LOGL, int SIGN, int PER = 32, class Tw>
 __device__ __forceinline__ void team_pass2(int tt, const float2* __restrict__ buf, Tw tw,
                                            float2* __restrict__ res) {
-  using T = Team<LOGL>;
+  using T = Team<LOGL, PER>;
 #pragma unroll
   for (int i = 0; i < T::J2; ++i) {
     const int j = tt + T::TT * i;
@@ -254,9 +254,9 @@ __device__ __forceinline__ void stockham_pass(int tt, In in, Tw tw, Sync sync, O
 }
 
 // Element index of res[i * R2 + r] after team_pass2.
-template <int LOGL>
+template <int LOGL, int PER = 32>
 __device__ __forceinline__ int team_out_index(int tt, int i, int r) {
-  using T = Team<LOGL>;
+  using T = Team<LOGL, PER>;
   return tt + T::TT * i + r * T::R1;
 }
 

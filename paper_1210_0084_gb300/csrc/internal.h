@@ -19,7 +19,8 @@ constexpr int kPerThread = 32;
 constexpr int kMaxTwoPassLog2 = 10;  // M_k <= 1024: two register passes of <= 32
 constexpr int kMaxBandLog2 = 12;     // M_k <= 4096: three passes (16, 16, <= 16)
 constexpr int kMinBandLog2 = 4;   // M_k >= 16
-constexpr int kSliceMaxThreads = 256;  // slice kernels: N / (32 C) <= 256
+constexpr int kSliceMaxThreads = 256;  // slice kernels: N / (kSlicePer C) <= 256
+constexpr int kSlicePer = 32;          // complex values a slice-kernel thread holds
 constexpr int64_t kMaxGridY = 65535;
 // shared memory (complex values) a band group's synthesis may use for its
 // twiddles, team buffers and accumulator layers; a group closes before

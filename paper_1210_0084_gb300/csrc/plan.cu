@@ -325,9 +325,10 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
   int C = p->slice_cluster;
   if (C == 0) {
     C = 1;
-    while (N / C > 32 * kSliceMaxThreads) C <<= 1;
+    while (N / C > kSlicePer * kSliceMaxThreads) C <<= 1;
   }
-  if (N / C > 32 * kSliceMaxThreads || (1 << pl->logP) < C || N / (32 * C) < 1) return SLICQ_EUNSUPPORTED;
+  if (N / C > kSlicePer * kSliceMaxThreads || (1 << pl->logP) < C || N / (kSlicePer * C) < 1 || C > 8)
+    return SLICQ_EUNSUPPORTED;
   pl->C = C;
   {
     const int P = 1 << pl->logP, Qn = 1 << pl->logQ;
@@ -533,16 +534,16 @@ cudaError_t upload_lanes(slicq_plan* pl, bool synthesis, const std::vector<int>&
 // Lanes per group from measured costs: both persistent band kernels run on
 // zeros (the timing does not depend on the values) with the same number of
 // lanes per group, first once to warm caches and clocks (one slice per
-// lane), then three times with six slices per lane; a group's cost is the
-// median over the three runs of its CTAs' SM clocks per slice.  The plan
+// lane), then five times with eight slices per lane; a group's cost is the
+// median over the five runs of its CTAs' SM clocks per slice.  The plan
 // keeps its estimated lanes if any step fails.
 void calibrate_lanes(slicq_plan* pl) {
-  constexpr int kRuns = 3;
+  constexpr int kRuns = 5;
   const int G = pl->G;
   // the same lanes per group for both kernels, within both kernels' slots
   const int per = std::max(1, std::min(pl->slots_a, pl->slots_s) / G);
   const std::vector<int> equal(G, per);
-  const int64_t S = 6 * (int64_t)per;
+  const int64_t S = 8 * (int64_t)per;
   Workspace ws;
   const size_t wbytes = workspace_layout_rows(pl, S, nullptr, &ws);
   const size_t cbytes = sizeof(float2) * (size_t)(S * pl->coefs_per_slice);

@@ -80,8 +80,8 @@ __device__ __forceinline__ void row_of(const SliceArgs& a, int64_t s, int64_t& s
 template <int LOGP, int LOGQ>
 struct Geo {
   static constexpr int P = 1 << LOGP, Q = 1 << LOGQ;
-  using TP = Team<LOGP>;
-  using TQ = Team<LOGQ>;
+  using TP = Team<LOGP, kSlicePer>;
+  using TQ = Team<LOGQ, kSlicePer>;
   static constexpr int CS1 = TP::BUF;      // odd column stride of pass buffers
   static constexpr int XS1 = P + 1;        // column stride of the exchange layout
   static constexpr int CS3 = TQ::BUF;
@@ -148,17 +148,17 @@ __device__ __forceinline__ void fourstep(const SliceArgs& a, cg::cluster_group& 
     const int tt = t >> a.logQc;
     const int q = rank * Qc + ql;
     float2* buf = sm + ql * G::CS1;
-    team_pass1<LOGP, SIGN>(tt, buf, [&](int p) { return load(p * G::Q + q); });
+    team_pass1<LOGP, SIGN, kSlicePer>(tt, buf, [&](int p) { return load(p * G::Q + q); });
     __syncthreads();
     float2 col[TP::HELD];
-    team_pass2<LOGP, SIGN>(tt, buf, PassTw<LOGP, SIGN>{tabs.twP}, col);
+    team_pass2<LOGP, SIGN, kSlicePer>(tt, buf, PassTw<LOGP, SIGN>{tabs.twP}, col);
     __syncthreads();
     // four-step twiddle W_N^{q u} = W_2N^{2 q u}, then the exchange layout [ql][u]
 #pragma unroll
     for (int i = 0; i < TP::J2; ++i)
 #pragma unroll
       for (int r = 0; r < TP::R2; ++r) {
-        const int u = team_out_index<LOGP>(tt, i, r);
+        const int u = team_out_index<LOGP, kSlicePer>(tt, i, r);
         float2 w = __ldg(a.tw4 + u * G::Q + q);
         if (SIGN > 0) w.y = -w.y;
         sm[ql * G::XS1 + u] = c_mul(col[i * TP::R2 + r], w);
@@ -198,7 +198,7 @@ __device__ __forceinline__ void fourstep(const SliceArgs& a, cg::cluster_group& 
       for (int r = 0; r < TQ::R1; ++r) buf[TQ::pad1(j, r)] = v[r];
     }
     __syncthreads();
-    team_pass2<LOGQ, SIGN>(tt, buf, PassTw<LOGQ, SIGN>{tabs.twQ}, res);
+    team_pass2<LOGQ, SIGN, kSlicePer>(tt, buf, PassTw<LOGQ, SIGN>{tabs.twQ}, res);
   }
   ul_out = ul;
   tt_out = tt;
@@ -207,7 +207,7 @@ __device__ __forceinline__ void fourstep(const SliceArgs& a, cg::cluster_group& 
 // ------------------------------------------------------------- forward ---
 
 template <int LOGP, int LOGQ>
-__global__ void __launch_bounds__(kSliceMaxThreads, 2) slice_forward_kernel(SliceArgs a) {
+__global__ void __launch_bounds__(kSliceMaxThreads, kSlicePer == 16 ? 3 : 2) slice_forward_kernel(SliceArgs a) {
   using G = Geo<LOGP, LOGQ>;
   using TQ = typename G::TQ;
   extern __shared__ float2 sm[];
@@ -261,7 +261,7 @@ __global__ void __launch_bounds__(kSliceMaxThreads, 2) slice_forward_kernel(Slic
     for (int i = 0; i < TQ::J2; ++i)
 #pragma unroll
       for (int r = 0; r < TQ::R2; ++r)
-        sm[team_out_index<LOGQ>(tt, i, r) * Pc + ul] = res[i * TQ::R2 + r];  // [v][ul]
+        sm[team_out_index<LOGQ, kSlicePer>(tt, i, r) * Pc + ul] = res[i * TQ::R2 + r];  // [v][ul]
   }
   cluster.sync();
 
@@ -302,7 +302,7 @@ __global__ void __launch_bounds__(kSliceMaxThreads, 2) slice_forward_kernel(Slic
 // ------------------------------------------------------------- inverse ---
 
 template <int LOGP, int LOGQ>
-__global__ void __launch_bounds__(kSliceMaxThreads, 2) slice_inverse_kernel(SliceArgs a) {
+__global__ void __launch_bounds__(kSliceMaxThreads, kSlicePer == 16 ? 3 : 2) slice_inverse_kernel(SliceArgs a) {
   using G = Geo<LOGP, LOGQ>;
   using TQ = typename G::TQ;
   extern __shared__ float2 sm[];
@@ -338,7 +338,7 @@ __global__ void __launch_bounds__(kSliceMaxThreads, 2) slice_inverse_kernel(Slic
 #pragma unroll
     for (int i = 0; i < TQ::J2; ++i)
 #pragma unroll
-      for (int r = 0; r < TQ::R2; ++r) sm[ul * G::ZS3 + team_out_index<LOGQ>(tt, i, r)] = res[i * TQ::R2 + r];
+      for (int r = 0; r < TQ::R2; ++r) sm[ul * G::ZS3 + team_out_index<LOGQ, kSlicePer>(tt, i, r)] = res[i * TQ::R2 + r];
   }
   __syncthreads();
 
@@ -429,7 +429,7 @@ cudaError_t launch_slice(bool forward, const slicq_plan* pl, const SliceArgs& a,
   void (*kern)(SliceArgs) = forward ? slice_forward_kernel<LOGP, LOGQ> : slice_inverse_kernel<LOGP, LOGQ>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, pl->slice_smem);
   if (e != cudaSuccess) return e;
-  const int threads = (1 << (LOGP + LOGQ)) / (32 * pl->C);
+  const int threads = (1 << (LOGP + LOGQ)) / (kSlicePer * pl->C);
   cudaLaunchConfig_t cfg{};
   cfg.gridDim = dim3((unsigned)(slices * pl->C));
   cfg.blockDim = dim3(threads);
