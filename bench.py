@@ -14,6 +14,10 @@ between timed steps, outside the per-step CUDA events.  N > 1 runs N
 independent replicas (one clip per GPU; the transform has no exchange step).
 --impl reference times the FP64 CPU oracle (the only other implementation
 of the method) on the host cores instead.
+
+Beside the step the line reports the sliCQ spectrogram epilogue, the
+streaming mode's per-call latency and the differentiation workload
+(multi-resolution log-magnitude loss and its backward through the adjoint).
 """
 
 from __future__ import annotations
@@ -238,6 +242,79 @@ def _config(world, mk_policy="pow2"):
             "samples_per_channel": WORKLOAD["seconds"] * int(WORKLOAD["fs"]),
             "mk_policy": mk_policy, "l2": "flushed between timed steps (256 MiB write, outside the events)",
             "parallelism": f"replicas x{world} (independent clips, no exchange)"}
+
+
+def differentiation(dev, stream, flush, peak, steps=10, warmup=3):
+    """Differentiation workload: batch 32 x 6 s mono at 44.1 kHz (noisy/clean
+    tone mixtures), multi-resolution log-magnitude L1 loss over B = 12, 24, 48
+    (fmin 40 Hz, fmax 22050 Hz, 2N 8192, M 2048, eps 1e-6).  One step =
+    three forward transforms of the noisy batch through slicq_transform,
+    three of the clean batch, the loss (torch elementwise ops) and its
+    backward (three slicq_adjoint calls).  Also timed: the nine transforms
+    alone on the same buffers, so the loss arithmetic's share is visible."""
+    import torch
+    from paper_1210_0084_gb300 import signals
+    from paper_1210_0084_gb300.slicq import SliCQParams, SliCQPlan, slicq_transform
+
+    fs, n, batch, eps = 44100.0, 6 * 44100, 32, 1e-6
+    noisy, clean = signals.noisy_clean_tone_mixtures(batch, n, fs, seed=signals.seed_for(4))
+    plans = [SliCQPlan(SliCQParams(fs, 40.0, fs / 2, B, 8192, 2048), dev.index) for B in (12, 24, 48)]
+    xt = torch.from_numpy(noisy).to(dev)
+    tt = torch.from_numpy(clean).to(dev)
+
+    def step():
+        x = xt.detach().requires_grad_(True)
+        loss = 0.0
+        for p in plans:
+            c = slicq_transform(x, p)
+            with torch.no_grad():
+                ct = p.forward(tt)
+            loss = loss + (torch.log(c.abs() + eps) - torch.log(ct.abs() + eps)).abs().mean()
+        loss.backward()
+        return loss
+
+    coefs = [torch.empty((batch, p.num_slices(n), p.coefs_per_slice), dtype=torch.complex64, device=dev)
+             for p in plans]
+    ct_buf = [torch.empty_like(c) for c in coefs]
+    g_buf = torch.empty((batch, n), dtype=torch.float32, device=dev)
+
+    def transforms():
+        for p, c, ct in zip(plans, coefs, ct_buf):
+            p.forward(xt, out=c)
+            p.forward(tt, out=ct)
+            p.adjoint(c, n, out=g_buf)
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        ms = []
+        for i in range(steps):
+            flush.fill_(i & 255)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return statistics.median(ms)
+
+    step_ms = timed(step)
+    tr_ms = timed(transforms)
+    # algorithmic bytes of the nine transforms: forward 4 + 8 cps/N per input
+    # sample, adjoint 8 cps/N + 4 (per resolution, noisy forward + clean
+    # forward + adjoint)
+    tr_bytes = 0
+    for p in plans:
+        S, cps = p.num_slices(n), p.coefs_per_slice
+        tr_bytes += 3 * batch * (4 * n + 8 * S * cps)
+    return {"workload": "batch 32 x 6 s mono 44.1 kHz, noisy/clean tone mixtures; log-magnitude L1 "
+                        "loss over B = 12, 24, 48 (fmin 40 Hz, 2N 8192, M 2048); custom backward",
+            "ms_per_step": step_ms, "samples_per_s": batch * n / (step_ms * 1e-3),
+            "transforms_ms": tr_ms, "transforms_alg_bytes": tr_bytes,
+            "transforms_gbs": tr_bytes / (tr_ms * 1e-3) / 1e9,
+            "transforms_frac": tr_bytes / (tr_ms * 1e-3) / 1e9 / peak,
+            "loss_share": max(0.0, 1.0 - tr_ms / step_ms)}
 
 
 # ---------------------------------------------------------------- native ---
@@ -476,6 +553,8 @@ def main():
                  "delay_samples": "one slice: output lags input by N - a0 - 1 after a slice's block"}
     del sst
 
+    diff = differentiation(dev, stream, flush, peak)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         cpu = cpu_baseline(x)
@@ -487,7 +566,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": _config(world, args.mk_policy), "recon_rel_err": recon_err,
             "roofline": roofline, "step_roofline": step_roof, "kernels": kern, "epilogues": epilogues,
-            "streaming": streaming,
+            "streaming": streaming, "differentiation": diff,
             "gpu_launches": len(traced), "e2e": e2e, "cpu_baseline": cpu,
             "clocks": sampler.summary(), "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms),
         }

@@ -283,3 +283,60 @@ def test_inverse_modified_shift_needs_rectangular(S):
     c = plan.forward(torch.zeros(4096, device="cuda"))
     with pytest.raises(S.SliCQError):
         plan.inverse_modified(c, 4096, shift=2)
+
+
+def test_multires_logmag_loss_backward(S):
+    """Differentiation workload in small: L = sum_B mean |log(|c_B(x)| + eps) -
+    log(|c_B(t)| + eps)| over B = 12, 24, 48 (fmin 40 Hz, 2N = 8192, M = 2048),
+    batch 3 of noisy/clean tone mixtures.  The gradient torch computes through
+    slicq_transform must equal, per resolution, the oracle's adjoint (FP64) of
+    the same upstream gradient dL/dc, summed over resolutions; the loss must
+    match the oracle's coefficients' loss.
+
+    Scale of the bound: the upstream gradient of a log-magnitude loss weights
+    each coefficient by 1/|c|.  The slices over the zero padding (n = 20000
+    is padded to L = 24576) hold tiny coefficients, so their weights
+    dominate, and their share of the adjoint lands in the padding, which the
+    output drops: the adjoint over all L samples is 450-1100 times larger
+    than the trimmed gradient.  A float32 linear map's error scales with the
+    values it adds up, so the error is bounded by REL times the norm of the
+    untrimmed adjoint (the oracle's adjoint with output length L).  An
+    adjoint mistake is still ~1e-3 of that scale; the random-coefficient
+    parity tests check the adjoint against its output's own norm."""
+    fs, n, batch, eps = 44100.0, 20000, 3, 1e-6
+    noisy, clean = signals.noisy_clean_tone_mixtures(batch, n, fs, seed=signals.seed_for(4, 1))
+    plans = [S.SliCQPlan(S.SliCQParams(fs, 40.0, fs / 2, B, 8192, 2048)) for B in (12, 24, 48)]
+    xt = torch.from_numpy(noisy).cuda().requires_grad_(True)
+    tt = torch.from_numpy(clean).cuda()
+    cs, cts, loss = [], [], 0.0
+    for plan in plans:
+        c = S.slicq_transform(xt, plan)
+        c.retain_grad()
+        ct = plan.forward(tt)
+        loss = loss + (torch.log(c.abs() + eps) - torch.log(ct.abs() + eps)).abs().mean()
+        cs.append(c)
+        cts.append(ct)
+    loss.backward()
+    g = xt.grad.cpu().numpy().astype(np.float64)
+    gref = np.zeros_like(g)
+    lgpu, lref, scale2 = 0.0, 0.0, 0.0
+    for plan, c, ct in zip(plans, cs, cts):
+        op = _oplan(plan.params)
+        up = c.grad.cpu().numpy().astype(np.complex128)
+        L = O.padded_length(n, plan.params.slice_len)
+        for b in range(batch):
+            gref[b] += O.slicq_adjoint(up[b], op, n)
+            scale2 += float(np.sum(O.slicq_adjoint(up[b], op, L) ** 2))
+        cn = np.stack([O.slicq_forward(noisy[b].astype(np.float64), op) for b in range(batch)])
+        cc = np.stack([O.slicq_forward(clean[b].astype(np.float64), op) for b in range(batch)])
+        # the loss value over the coefficients float32 resolves: those of the
+        # zero padding and far from the clean mixture's tones lie near its
+        # rounding floor (~1e-7 max|c|), where log(|c| + eps) moves by O(1)
+        keep = (np.abs(cn) > 1e-3 * np.abs(cn).max()) & (np.abs(cc) > 1e-3 * np.abs(cc).max())
+        dn = c.detach().cpu().numpy().astype(np.complex128)
+        dc = ct.cpu().numpy().astype(np.complex128)
+        lgpu += np.mean(np.abs(np.log(np.abs(dn[keep]) + eps) - np.log(np.abs(dc[keep]) + eps)))
+        lref += np.mean(np.abs(np.log(np.abs(cn[keep]) + eps) - np.log(np.abs(cc[keep]) + eps)))
+    err = float(np.linalg.norm(g - gref))
+    assert err <= REL * np.sqrt(scale2), (err, np.sqrt(scale2))
+    assert abs(lgpu - lref) <= 1e-4 * lref, (lgpu, lref)
