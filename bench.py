@@ -16,8 +16,9 @@ independent replicas (one clip per GPU; the transform has no exchange step).
 of the method) on the host cores instead.
 
 Beside the step the line reports the sliCQ spectrogram epilogue, the
-streaming mode's per-call latency and the differentiation workload
-(multi-resolution log-magnitude loss and its backward through the adjoint).
+streaming mode's per-call latency, the differentiation workload
+(multi-resolution log-magnitude loss and its backward through the adjoint)
+and the split-precision tensor-core band DFTs against the FP32 form.
 """
 
 from __future__ import annotations
@@ -317,6 +318,74 @@ def differentiation(dev, stream, flush, peak, steps=10, warmup=3):
             "loss_share": max(0.0, 1.0 - tr_ms / step_ms)}
 
 
+def precision_compare(dev, stream, flush, x_stereo, steps=10, warmup=3):
+    """The plain FP32 form against the split-precision tensor-core band DFTs
+    (FP16 and BF16 hi + lo), forward + inverse at equal inputs: the headline
+    60 s stereo workload and the 10 min mono 48 kHz workload (B = 96,
+    fmin 27.5 Hz, fmax 24 kHz, 2N 131072, M 32768; noise + exponential
+    chirps).  Per precision: ms per step, samples/s, reconstruction error,
+    and the traced band-kernel times."""
+    import torch
+    from paper_1210_0084_gb300 import signals
+    from paper_1210_0084_gb300.slicq import SliCQParams, SliCQPlan
+
+    n10 = 600 * 48000
+    x10 = signals.noise_plus_chirps(n10, 48000.0, seed=signals.seed_for(3))[None]
+    workloads = [
+        ("60 s stereo 44.1 kHz, B 48, 2N 65536", x_stereo,
+         (WORKLOAD["fs"], WORKLOAD["fmin"], WORKLOAD["fmax"], WORKLOAD["bins_per_octave"],
+          WORKLOAD["slice_len"], WORKLOAD["trans_len"])),
+        ("10 min mono 48 kHz, B 96, fmin 27.5 Hz, 2N 131072, M 32768", x10,
+         (48000.0, 27.5, 24000.0, 96, 131072, 32768)),
+    ]
+    out = []
+    for name, x, prm in workloads:
+        xd = torch.from_numpy(x).to(dev)
+        batch, n = x.shape
+        res = {"workload": name, "samples": batch * n}
+        for prec in ("fp32", "split_fp16", "split_bf16"):
+            plan = SliCQPlan(SliCQParams(*prm, precision=prec), dev.index)
+            S = plan.num_slices(n)
+            c = torch.empty((batch, S, plan.coefs_per_slice), dtype=torch.complex64, device=dev)
+            y = torch.empty((batch, n), dtype=torch.float32, device=dev)
+            for _ in range(warmup):
+                plan.forward(xd, out=c)
+                plan.inverse(c, n, out=y)
+            torch.cuda.synchronize()
+            ms = []
+            for i in range(steps):
+                flush.fill_(i & 255)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                plan.forward(xd, out=c)
+                plan.inverse(c, n, out=y)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            plan.trace(True)
+            for i in range(steps):
+                flush.fill_(i & 255)
+                plan.forward(xd, out=c)
+                plan.inverse(c, n, out=y)
+            torch.cuda.synchronize()
+            per = {}
+            for k, t in plan.trace_read():
+                per.setdefault(k, []).append(t)
+            plan.trace(False)
+            plan.check()
+            med = statistics.median(ms)
+            res[prec] = {"ms_per_step": med, "samples_per_s": batch * n / (med * 1e-3),
+                         "recon_rel_err": float(torch.linalg.norm(y - xd) / torch.linalg.norm(xd)),
+                         "band_analysis_ms": statistics.mean(per.get("band_analysis", [0.0])),
+                         "band_synthesis_ms": statistics.mean(per.get("band_synthesis", [0.0]))}
+            del plan, c, y
+        for prec in ("split_fp16", "split_bf16"):
+            res[prec]["speedup_vs_fp32"] = res["fp32"]["ms_per_step"] / res[prec]["ms_per_step"]
+        out.append(res)
+        del xd
+    return out
+
+
 # ---------------------------------------------------------------- native ---
 
 def main():
@@ -554,6 +623,7 @@ def main():
     del sst
 
     diff = differentiation(dev, stream, flush, peak)
+    prec_cmp = precision_compare(dev, stream, flush, x)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -566,7 +636,7 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": _config(world, args.mk_policy), "recon_rel_err": recon_err,
             "roofline": roofline, "step_roofline": step_roof, "kernels": kern, "epilogues": epilogues,
-            "streaming": streaming, "differentiation": diff,
+            "streaming": streaming, "differentiation": diff, "precision": prec_cmp,
             "gpu_launches": len(traced), "e2e": e2e, "cpu_baseline": cpu,
             "clocks": sampler.summary(), "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms),
         }

@@ -43,7 +43,7 @@
 extern "C" {
 #endif
 
-#define SLICQ_ABI_VERSION 1
+#define SLICQ_ABI_VERSION 2
 
 #if defined(__GNUC__)
 #define SLICQ_API __attribute__((visibility("default")))
@@ -70,6 +70,11 @@ typedef enum {                                             /* M_k choice */
   SLICQ_MK_MULT4 = 1,  /* smallest multiple of 4 >= |J_k|: not built (EUNSUPPORTED) */
   SLICQ_MK_CONST = 2   /* one M for every channel: the rectangular representation */
 } slicq_mk_policy;
+typedef enum {                                             /* band-transform arithmetic */
+  SLICQ_PREC_FP32 = 0,        /* every DFT stage in FP32 on the CUDA cores */
+  SLICQ_PREC_SPLIT_FP16 = 1,  /* radix-8/16/32 stages of the band DFTs on the tensor cores: FP16 hi + lo */
+  SLICQ_PREC_SPLIT_BF16 = 2   /* the same with BF16 hi + lo */
+} slicq_precision;
 
 /*
  * Parameters of one sliCQ system (Sec. 3 and Sec. 4).
@@ -90,6 +95,16 @@ typedef enum {                                             /* M_k choice */
  *                    rectangular representation, L/a_k constant, Sec. 4.1).
  *   slice_cluster    CTAs per slice FFT (thread-block cluster size); 0 picks
  *                    the default.  Must be a power of two <= 8 if given.
+ *   precision        arithmetic of the band DFTs of length M_k (Algorithm 1's
+ *                    IFFT_{M_k}, Algorithm 2's FFT_{M_k}) for M_k <= 1024:
+ *                    SLICQ_PREC_FP32, or a split-precision tensor-core form
+ *                    in which each radix-8/16/32 stage is a product of
+ *                    (hi + lo) operands in FP16 or BF16 with FP32
+ *                    accumulation (three of the four partial products;
+ *                    rows scaled by powers of two first).  FP16 pairs keep
+ *                    22 significant bits (about FP32's accuracy), BF16 pairs
+ *                    16.  Slice FFTs, windows and M_k = 2048, 4096 stay FP32.
+ *                    Plan tables (duals, twiddles) are FP64-computed either way.
  */
 typedef struct {
   double fs;
@@ -102,7 +117,7 @@ typedef struct {
   int32_t window;
   int32_t mk_policy;
   int32_t slice_cluster;
-  int32_t reserved;
+  int32_t precision;
 } slicq_params;
 
 typedef struct slicq_plan slicq_plan;
@@ -144,6 +159,16 @@ SLICQ_API slicq_status slicq_layout_tables(const slicq_params* p, int32_t n_chan
 SLICQ_API slicq_status slicq_plan_create(const slicq_params* p, int device,
                                slicq_plan** out);
 SLICQ_API void slicq_plan_destroy(slicq_plan* plan);
+
+/*
+ * Device-side status of a plan's launches so far.  Synchronises the plan's
+ * device, then returns SLICQ_ETIMEOUT (and clears it) if a band kernel of
+ * a split-precision plan gave up waiting for its tensor-core products
+ * (each wait is bounded, about one second; the kernel then stops and frees
+ * its tensor memory, and its outputs are incomplete), SLICQ_ECUDA if the
+ * device reports an error, SLICQ_OK otherwise.  FP32 plans never time out.
+ */
+SLICQ_API slicq_status slicq_plan_check(const slicq_plan* plan);
 
 /* K + 2 and sum_k M_k of a plan. */
 SLICQ_API slicq_status slicq_plan_info(const slicq_plan* plan, int32_t* n_channels,

@@ -180,6 +180,19 @@ slicq_status slicq_plan_create(const slicq_params* p, int device, slicq_plan** o
 
 void slicq_plan_destroy(slicq_plan* plan) { free_plan(plan); }
 
+slicq_status slicq_plan_check(const slicq_plan* plan) {
+  if (!plan) return SLICQ_EINVAL;
+  return on_device(plan, [&]() -> slicq_status {
+    if (cudaDeviceSynchronize() != cudaSuccess) return SLICQ_ECUDA;
+    int flag = 0;
+    if (cudaMemcpy(&flag, plan->d_err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return SLICQ_ECUDA;
+    if (!flag) return SLICQ_OK;
+    const int zero = 0;
+    if (cudaMemcpy(plan->d_err, &zero, sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess) return SLICQ_ECUDA;
+    return SLICQ_ETIMEOUT;
+  });
+}
+
 slicq_status slicq_plan_info(const slicq_plan* plan, int32_t* n_channels, int64_t* coefs_per_slice) {
   if (!plan) return SLICQ_EINVAL;
   if (n_channels) *n_channels = plan->n_channels;

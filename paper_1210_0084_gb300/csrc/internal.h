@@ -144,6 +144,7 @@ struct slicq_plan {
   float2* d_twband = nullptr; // band pass-2 twiddles, per length, [r][j] layout
   float2* d_tw4 = nullptr;    // four-step twiddles exp(-2 pi i q u / N) at [u Q + q]
   float2* d_tw4096 = nullptr; // exp(-2 pi i t / 4096), t < 4096
+  int* d_err = nullptr;       // 1 once a split-precision band kernel gave up a tensor-core wait
 
   // optional kernel timing trace (events around every launch)
   struct Trace {

@@ -20,6 +20,7 @@
 
 #include "fft_common.cuh"
 #include "internal.h"
+#include "tc_dft.cuh"
 
 namespace slicq {
 
@@ -42,6 +43,9 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
   if (p->window != SLICQ_WIN_HANN && p->window != SLICQ_WIN_BLACKMAN_HARRIS) return SLICQ_EINVAL;
   if (p->mk_policy == SLICQ_MK_MULT4) return SLICQ_EUNSUPPORTED;  // band FFTs are radix-2
   if (p->mk_policy != SLICQ_MK_POW2 && p->mk_policy != SLICQ_MK_CONST) return SLICQ_EINVAL;
+  if (p->precision != SLICQ_PREC_FP32 && p->precision != SLICQ_PREC_SPLIT_FP16 &&
+      p->precision != SLICQ_PREC_SPLIT_BF16)
+    return SLICQ_EINVAL;
   const int64_t L2 = p->slice_len;
   if (!is_pow2(L2)) return SLICQ_EINVAL;
   if (L2 < 2048 || L2 > 131072) return SLICQ_EUNSUPPORTED;
@@ -162,7 +166,16 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
   // ---- band groups: consecutive channels, <= kBandThreads threads each
   pl->groups.clear();
   pl->thread_band.clear();
-  int smem_p = 0, syn_max = 0;  // complex values
+  size_t smem_p = 0, syn_max = 0;  // bytes
+  // split precision: a two-pass group of M >= 32 also holds its tensor-core
+  // region (operands, DFT matrices, mbarrier), 128-byte aligned after the
+  // rest of its shared memory
+  const bool split = p->precision != SLICQ_PREC_FP32;
+  auto tc_bytes = [&](int lm) { return split && lm >= 5 && lm <= kMaxTwoPassLog2 ? tc_region_bytes(lm) : 0; };
+  auto with_tc = [&](size_t cplx, int lm) {
+    const int tb = tc_bytes(lm);
+    return tb ? ((cplx * sizeof(float2) + 127) & ~(size_t)127) + (size_t)tb : cplx * sizeof(float2);
+  };
   pl->cost_a.clear();
   pl->cost_s.clear();
   {
@@ -201,7 +214,7 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
         const int lay = (int)(de.size() + me.size()) * acc_n;
         // synthesis shared memory: [pass-2 twiddles][team buffers][layers]
         const int need = ((lm > kMaxTwoPassLog2 ? 0 : M) + smem + need_s + 1 & ~1) + lay;
-        if (k > gd.band_begin && need > kSynSmemBudget) break;
+        if (k > gd.band_begin && with_tc((size_t)need, lm) > (size_t)kSynSmemBudget * sizeof(float2)) break;
         if (de.size() >= (size_t)kNoPhase || me.size() >= (size_t)kNoPhase) return SLICQ_EUNSUPPORTED;
         dend.swap(de);
         mend.swap(me);
@@ -245,8 +258,9 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
                                                     : M + (M >> ((gd.log2M + 1) / 2)) + 1;
         // synthesis: [pass-2 twiddles (two-pass lengths)][team buffers][layers]
         const int lay = ((gd.nphases & 0xFFFF) + (gd.nphases >> 16)) * (gd.acc_hi - gd.acc_lo);
-        syn_max = std::max(syn_max, (((gd.log2M > kMaxTwoPassLog2 ? 0 : M) + nb * bufl + 1) & ~1) + lay);
-        smem_p = std::max(smem_p, M + 2 * gd.fp_len + nb * bufl);
+        syn_max = std::max(syn_max, with_tc((size_t)((((gd.log2M > kMaxTwoPassLog2 ? 0 : M) + nb * bufl + 1) & ~1) + lay),
+                                            gd.log2M));
+        smem_p = std::max(smem_p, with_tc((size_t)(M + 2 * gd.fp_len + nb * bufl), gd.log2M));
         // estimated cycles per slice of one persistent CTA (a fixed part for
         // staging and barriers, the team transforms of the busiest warp
         // count times active warps, and the bin write-out); fitted to
@@ -313,8 +327,9 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
     if (gd.ex_hi < gd.ex_lo) gd.ex_hi = gd.ex_lo;
   }
   // per-slice band kernels: one team buffer per channel of the group
-  pl->band_smem_s = syn_max * (int)sizeof(float2);
-  pl->band_smem_p = smem_p * (int)sizeof(float2);
+  if (syn_max > 220 * 1024 || smem_p > 220 * 1024) return SLICQ_EUNSUPPORTED;
+  pl->band_smem_s = (int)syn_max;
+  pl->band_smem_p = (int)smem_p;
   if (pl->band_smem_p > 220 * 1024) return SLICQ_EUNSUPPORTED;
   if (pl->band_smem_s > 220 * 1024) return SLICQ_EUNSUPPORTED;
 
@@ -649,6 +664,7 @@ slicq_status build_tables(slicq_plan* pl) {
   const size_t o_twband = take(sizeof(float2) * 2032);
   const size_t o_tw4 = take(sizeof(float2) * pl->N);
   const size_t o_tw4096 = take(sizeof(float2) * 4096);
+  const size_t o_err = take(sizeof(int));
   if (cudaMalloc(&pl->d_arena, off) != cudaSuccess) return SLICQ_ENOMEM;
   char* base = (char*)pl->d_arena;
   pl->d_bands = (BandDesc*)(base + o_bands);
@@ -672,6 +688,7 @@ slicq_status build_tables(slicq_plan* pl) {
   pl->d_twband = (float2*)(base + o_twband);
   pl->d_tw4 = (float2*)(base + o_tw4);
   pl->d_tw4096 = (float2*)(base + o_tw4096);
+  pl->d_err = (int*)(base + o_err);
 
   slicq_status st = SLICQ_OK;
   cudaError_t e = cudaSuccess;
@@ -680,7 +697,8 @@ slicq_status build_tables(slicq_plan* pl) {
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, pl->device) == cudaSuccess && sms > 0)
       pl->num_sms = sms;
   }
-  e = cudaMemcpy(pl->d_bands, pl->bands.data(), sizeof(BandDesc) * nch, cudaMemcpyHostToDevice);
+  e = cudaMemset(pl->d_err, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemcpy(pl->d_bands, pl->bands.data(), sizeof(BandDesc) * nch, cudaMemcpyHostToDevice);
   if (e == cudaSuccess)
     e = cudaMemcpy(pl->d_groups, pl->groups.data(), sizeof(GroupDesc) * pl->G, cudaMemcpyHostToDevice);
   if (e == cudaSuccess)

@@ -51,7 +51,7 @@ class _Params(ctypes.Structure):
                 ("bins_per_octave", ctypes.c_int32), ("min_filter_len", ctypes.c_int32),
                 ("slice_len", ctypes.c_int64), ("trans_len", ctypes.c_int64),
                 ("window", ctypes.c_int32), ("mk_policy", ctypes.c_int32),
-                ("slice_cluster", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("slice_cluster", ctypes.c_int32), ("precision", ctypes.c_int32)]
 
 
 _lib = None
@@ -77,6 +77,7 @@ def load_library():
         "slicq_plan_create": (ctypes.c_int, [P, ctypes.c_int, ctypes.POINTER(VP)]),
         "slicq_plan_destroy": (None, [VP]),
         "slicq_plan_info": (ctypes.c_int, [VP, ctypes.POINTER(I32), ctypes.POINTER(I64)]),
+        "slicq_plan_check": (ctypes.c_int, [VP]),
         "slicq_num_slices": (I64, [VP, I64]),
         "slicq_workspace_size": (ctypes.c_int, [VP, I64, I64, ctypes.POINTER(SZ)]),
         "slicq_forward": (ctypes.c_int, [VP, VP, I64, I64, VP, I64, VP, SZ, VP]),
@@ -127,14 +128,16 @@ class SliCQParams:
     slice_cluster: int = 0
     mk_policy: str = "pow2"   # "pow2" or "const" (rectangular representation)
     window: str = "hann"      # "hann" or "blackman_harris"
+    precision: str = "fp32"   # "fp32", "split_fp16" or "split_bf16" (band DFT stages)
 
     def to_c(self) -> _Params:
         mk = {"pow2": 0, "mult4": 1, "const": 2}[self.mk_policy]
         win = {"hann": 0, "blackman_harris": 1}[self.window]
+        prec = {"fp32": 0, "split_fp16": 1, "split_bf16": 2}[self.precision]
         return _Params(float(self.fs), float(self.fmin), float(self.fmax),
                        int(self.bins_per_octave), int(self.min_filter_len),
                        int(self.slice_len), int(self.trans_len), win, mk,
-                       int(self.slice_cluster), 0)
+                       int(self.slice_cluster), prec)
 
 
 def layout(p: SliCQParams) -> Dict[str, np.ndarray]:
@@ -189,6 +192,11 @@ class SliCQPlan:
     @property
     def handle(self) -> ctypes.c_void_p:
         return self._h
+
+    def check(self):
+        """Synchronise and raise SliCQError if a launch of this plan reported a
+        device-side failure (a split-precision tensor-core wait that gave up)."""
+        _check(self.lib.slicq_plan_check(self._h), "slicq_plan_check")
 
     def num_slices(self, n: int) -> int:
         return int(self.lib.slicq_num_slices(self._h, int(n)))

@@ -30,7 +30,7 @@ def test_exports_every_declared_symbol(lib, repo_root):
     assert len(names) >= 12
     for n in names:
         assert hasattr(lib, n), n
-    assert lib.slicq_abi_version() == 1
+    assert lib.slicq_abi_version() == 2
 
 
 def test_status_strings(lib):
