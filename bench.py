@@ -400,6 +400,9 @@ def main():
                     help="skip the 1 s load phases around the timed region (for profiler runs)")
     ap.add_argument("--mk-policy", choices=("pow2", "const"), default="pow2",
                     help="band lengths: pow2 (headline) or const (rectangular representation)")
+    ap.add_argument("--only-step", action="store_true",
+                    help="time the step and its kernels only (no e2e, epilogue, streaming, "
+                         "differentiation, precision or CPU measurements)")
     ap.add_argument("--workload", choices=("stereo60", "ragged"), default="stereo60",
                     help="stereo60: the headline workload; ragged: 256 clips over 16 plans "
                          "in one CUDA-graph replay per step")
@@ -544,6 +547,21 @@ def main():
     step_bytes = batch * (8 * n + 16 * S * cps)
     step_roof = {"alg_bytes": step_bytes, "achieved": step_bytes / (ms * 1e-3) / 1e9,
                  "frac": step_bytes / (ms * 1e-3) / 1e9 / peak}
+
+    if args.only_step:
+        if rank == 0:
+            print(json.dumps({
+                "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": _config(world, args.mk_policy), "recon_rel_err": recon_err,
+                "roofline": roofline, "step_roofline": step_roof, "kernels": kern,
+                "gpu_launches": len(traced), "clocks": sampler.summary(),
+                "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms)}), flush=True)
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
 
     # end to end through the public API with pinned host buffers
     xh = torch.from_numpy(x).pin_memory()

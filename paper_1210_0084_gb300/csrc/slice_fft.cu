@@ -131,7 +131,27 @@ __device__ __forceinline__ SliceTables stage_twiddles(const SliceArgs& a, float2
   return SliceTables{SmemTwiddles{lo, hi, a.tw.lb}, tp, tq};
 }
 
-template <int LOGP, int LOGQ, int SIGN, class Load>
+// Row u of phase 3 held at local slot ul of CTA `rank` when rows are
+// paired (PAIRED): the CTA holds rows rank H + w (w < H = Pc / 2) in slots
+// w and their partners P - (rank H + w) in slots H + w; CTA 0's row 0 is
+// its own partner, so its slot H holds the self-paired row P / 2.  The
+// even/odd split of the forward then finds every partner row locally.
+__device__ __forceinline__ int paired_row(int rank, int ul, int Pc, int P) {
+  const int H = Pc >> 1;
+  if (ul < H) return rank * H + ul;
+  const int x = rank * H + ul - H;
+  return x == 0 ? P / 2 : P - x;
+}
+
+// Local slot of the partner row (P - u, or u itself for u = 0, P / 2) of
+// the row in slot ul, paired layout.
+__device__ __forceinline__ int paired_partner_slot(int rank, int ul, int Pc) {
+  const int H = Pc >> 1;
+  if (rank == 0 && (ul == 0 || ul == H)) return ul;
+  return ul < H ? ul + H : ul - H;
+}
+
+template <int LOGP, int LOGQ, int SIGN, bool PAIRED, class Load>
 __device__ __forceinline__ void fourstep(const SliceArgs& a, cg::cluster_group& cluster,
                                          float2* sm, const SliceTables& tabs, Load load,
                                          float2* res, int& ul_out, int& tt_out) {
@@ -170,7 +190,7 @@ __device__ __forceinline__ void fourstep(const SliceArgs& a, cg::cluster_group& 
   const int Pc = 1 << a.logPc;
   const int ul = t & (Pc - 1);
   const int tt = t >> a.logPc;
-  const int u = rank * Pc + ul;
+  const int u = PAIRED ? paired_row(rank, ul, Pc, G::P) : rank * Pc + ul;
   {
     float2 v1[TQ::J1 * TQ::R1];
 #pragma unroll
@@ -252,34 +272,32 @@ __global__ void __launch_bounds__(kSliceMaxThreads, kSlicePer == 16 ? 3 : 2) sli
   {
     float2 res[TQ::HELD];
     int ul, tt;
-    fourstep<LOGP, LOGQ, -1>(a, cluster, sm, tabs, load, res, ul, tt);
+    fourstep<LOGP, LOGQ, -1, true>(a, cluster, sm, tabs, load, res, ul, tt);
     __syncthreads();
     // Z to shared memory, column-major [v][ul], for the even/odd split (needs
-    // Z[N - k] from the partner row): local reads, partner reads and the
-    // stores of X are then all contiguous across a warp
+    // Z[N - k] from the partner row, held by this CTA): local reads, partner
+    // reads and the stores of X are then all contiguous across a warp
 #pragma unroll
     for (int i = 0; i < TQ::J2; ++i)
 #pragma unroll
       for (int r = 0; r < TQ::R2; ++r)
         sm[team_out_index<LOGQ, kSlicePer>(tt, i, r) * Pc + ul] = res[i * TQ::R2 + r];  // [v][ul]
   }
-  cluster.sync();
+  __syncthreads();
 
   // X[k], k = u + P v for this CTA's rows u; X[N] from k = 0.  A thread keeps
   // one row u (fixed: idx & (Pc - 1) with blockDim a multiple of Pc), so its
-  // partner row P - u (row 0 for u = 0), the partner's CTA and e^{-2 pi i u / 2N}
-  // are computed once; e^{-2 pi i k / 2N} = e^{-2 pi i u / 2N} e^{-pi i v / Q}.
+  // partner row P - u (row 0 for u = 0), that row's local slot and
+  // e^{-2 pi i u / 2N} are computed once; e^{-2 pi i k / 2N} =
+  // e^{-2 pi i u / 2N} e^{-pi i v / Q}.
   const int rank = (int)cluster.block_rank();
   float2* X = a.spec + s * a.spec_stride;
   const int ul = threadIdx.x & (Pc - 1);
-  const int u = rank * Pc + ul;
-  const int up = u == 0 ? 0 : G::P - u;
-  const float2* psm = cluster.map_shared_rank(sm, up >> a.logPc) + (up & (Pc - 1));
+  const int u = paired_row(rank, ul, Pc, G::P);
+  const float2* psm = sm + paired_partner_slot(rank, ul, Pc);
   const float2 wu = tws((uint32_t)u);
   const float2* thalf = tabs.twQ + G::Q;  // e^{-pi i v / Q}, v < Q (staged after the Q table)
   const int vstep = (int)blockDim.x >> a.logPc;
-  // unrolled so that several partner loads from distributed shared memory
-  // are in flight at once
 #pragma unroll 8
   for (int v = (int)threadIdx.x >> a.logPc; v < G::Q; v += vstep) {
     const int vp = u == 0 ? ((G::Q - v) & (G::Q - 1)) : G::Q - 1 - v;
@@ -293,10 +311,6 @@ __global__ void __launch_bounds__(kSliceMaxThreads, kSlicePer == 16 ? 3 : 2) sli
     X[k] = c_add(E, c_mul(c_mul(wu, thalf[v]), O));
     if (k == 0) X[a.N] = c_sub(E, O);
   }
-  // keep this CTA's shared memory alive until its neighbours' partner loads
-  // are done (their values are consumed, so no memory ordering is needed)
-  asm volatile("barrier.cluster.arrive.relaxed.aligned;\n" ::: "memory");
-  asm volatile("barrier.cluster.wait.aligned;\n" ::: "memory");
 }
 
 // ------------------------------------------------------------- inverse ---
@@ -333,7 +347,7 @@ __global__ void __launch_bounds__(kSliceMaxThreads, kSlicePer == 16 ? 3 : 2) sli
   {
     float2 res[TQ::HELD];
     int ul, tt;
-    fourstep<LOGP, LOGQ, +1>(a, cluster, sm, tabs, load, res, ul, tt);
+    fourstep<LOGP, LOGQ, +1, false>(a, cluster, sm, tabs, load, res, ul, tt);
     __syncthreads();
 #pragma unroll
     for (int i = 0; i < TQ::J2; ++i)
