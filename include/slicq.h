@@ -170,6 +170,17 @@ SLICQ_API void slicq_plan_destroy(slicq_plan* plan);
  */
 SLICQ_API slicq_status slicq_plan_check(const slicq_plan* plan);
 
+/*
+ * What the plan chose by measurement at creation: the slice kernels'
+ * cluster size (CTAs per slice; with slice_cluster = 0 in the parameters the
+ * plan times every valid size on its device and keeps the fastest) and the
+ * number of persistent CTAs of the band analysis and synthesis kernels
+ * (their lanes per band group come from measured per-group costs).  Any
+ * pointer may be NULL.
+ */
+SLICQ_API slicq_status slicq_plan_tuning(const slicq_plan* plan, int32_t* slice_cluster,
+                                         int32_t* band_ctas_analysis, int32_t* band_ctas_synthesis);
+
 /* K + 2 and sum_k M_k of a plan. */
 SLICQ_API slicq_status slicq_plan_info(const slicq_plan* plan, int32_t* n_channels,
                              int64_t* coefs_per_slice);

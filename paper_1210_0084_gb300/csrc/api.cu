@@ -180,6 +180,15 @@ slicq_status slicq_plan_create(const slicq_params* p, int device, slicq_plan** o
 
 void slicq_plan_destroy(slicq_plan* plan) { free_plan(plan); }
 
+slicq_status slicq_plan_tuning(const slicq_plan* plan, int32_t* slice_cluster, int32_t* band_ctas_analysis,
+                               int32_t* band_ctas_synthesis) {
+  if (!plan) return SLICQ_EINVAL;
+  if (slice_cluster) *slice_cluster = plan->C;
+  if (band_ctas_analysis) *band_ctas_analysis = plan->n_cta_a;
+  if (band_ctas_synthesis) *band_ctas_synthesis = plan->n_cta_s;
+  return SLICQ_OK;
+}
+
 slicq_status slicq_plan_check(const slicq_plan* plan) {
   if (!plan) return SLICQ_EINVAL;
   return on_device(plan, [&]() -> slicq_status {

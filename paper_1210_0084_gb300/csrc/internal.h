@@ -160,6 +160,8 @@ namespace slicq {
 
 // Host layout (no device): fills everything in `pl` above the arena.
 slicq_status build_layout(const slicq_params* p, slicq_plan* pl);
+// Slice-kernel geometry (cluster size, shared-memory layout) for C CTAs per slice.
+void set_slice_cluster(slicq_plan* pl, int C);
 
 // Workspace partition for `rows` slice rows of a ragged batch (S = rows, L unused).
 size_t workspace_layout_rows(const slicq_plan* pl, int64_t rows, void* base, struct Workspace* ws);

@@ -344,22 +344,26 @@ slicq_status build_layout(const slicq_params* p, slicq_plan* pl) {
   }
   if (N / C > kSlicePer * kSliceMaxThreads || (1 << pl->logP) < C || N / (kSlicePer * C) < 1 || C > 8)
     return SLICQ_EUNSUPPORTED;
-  pl->C = C;
-  {
-    const int P = 1 << pl->logP, Qn = 1 << pl->logQ;
-    const int R2p = P / (1 << ((pl->logP + 1) / 2));
-    const int R2q = Qn / (1 << ((pl->logQ + 1) / 2));
-    const int cs1 = (Qn / C) * (P + R2p + 1);
-    const int xs1 = (Qn / C) * (P + 1);
-    const int cs3 = (P / C) * (Qn + R2q + 1);
-    const int zs3 = (P / C) * (Qn + 1);
-    pl->tw_lb = (ilog2_64(L2) + 1) / 2;
-    pl->slice_tw_off = std::max(std::max(cs1, xs1), std::max(cs3, zs3));
-    const int ntw = (1 << pl->tw_lb) + (int)(L2 >> pl->tw_lb);
-    // + the pass-2 tables of lengths P and Q and exp(-pi i v / Q), v < Q
-    pl->slice_smem = (pl->slice_tw_off + ntw + P + 2 * Qn) * (int)sizeof(float2);
-  }
+  pl->tw_lb = (ilog2_64(L2) + 1) / 2;
+  set_slice_cluster(pl, C);
   return SLICQ_OK;
+}
+
+// Slice-kernel geometry for a cluster of C CTAs: the shared-memory layout
+// [pass / exchange buffers][twiddle tables] of one CTA.
+void set_slice_cluster(slicq_plan* pl, int C) {
+  pl->C = C;
+  const int P = 1 << pl->logP, Qn = 1 << pl->logQ;
+  const int R2p = P / (1 << ((pl->logP + 1) / 2));
+  const int R2q = Qn / (1 << ((pl->logQ + 1) / 2));
+  const int cs1 = (Qn / C) * (P + R2p + 1);
+  const int xs1 = (Qn / C) * (P + 1);
+  const int cs3 = (P / C) * (Qn + R2q + 1);
+  const int zs3 = (P / C) * (Qn + 1);
+  pl->slice_tw_off = std::max(std::max(cs1, xs1), std::max(cs3, zs3));
+  const int ntw = (1 << pl->tw_lb) + (int)((2 * pl->N) >> pl->tw_lb);
+  // + the pass-2 tables of lengths P and Q and exp(-pi i v / Q), v < Q
+  pl->slice_smem = (pl->slice_tw_off + ntw + P + 2 * Qn) * (int)sizeof(float2);
 }
 
 // ----------------------------------------------------- FP64 table kernels ---
@@ -607,6 +611,58 @@ void calibrate_lanes(slicq_plan* pl) {
   upload_lanes(pl, true, balance_lanes(pl->cost_s, pl->slots_s));
 }
 
+// Slice cluster size from measurement (slice_cluster = 0): each valid C, from
+// the smallest that fits (N / C <= kSlicePer kSliceMaxThreads) up to 8, runs
+// the forward and inverse slice kernels (with the transition overlap-add) on
+// zeros over 2 x SMs slices: one warm-up run, then three timed runs; the
+// plan keeps the C with the smallest median.  It keeps the smallest C if any
+// step fails.
+void tune_slice_cluster(slicq_plan* pl) {
+  if (pl->params.slice_cluster != 0) return;
+  std::vector<int> cands;
+  for (int C = pl->C; C <= 8 && C <= (1 << pl->logP); C <<= 1) cands.push_back(C);
+  if (cands.size() < 2) return;
+  const int64_t L2 = 2 * pl->N;
+  const int64_t n = (int64_t)pl->num_sms * L2;  // 2 x SMs slices
+  const int C0 = pl->C;
+  Workspace ws;
+  const size_t wbytes = workspace_layout(pl, n, 1, nullptr, &ws);
+  float* x = nullptr;
+  float* y = nullptr;
+  void* work = nullptr;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  bool ok = cudaMalloc(&x, sizeof(float) * n) == cudaSuccess && cudaMalloc(&y, sizeof(float) * n) == cudaSuccess &&
+            cudaMalloc(&work, wbytes) == cudaSuccess && cudaMemset(x, 0, sizeof(float) * n) == cudaSuccess &&
+            cudaMemset(work, 0, wbytes) == cudaSuccess && cudaEventCreate(&e0) == cudaSuccess &&
+            cudaEventCreate(&e1) == cudaSuccess;
+  if (ok) workspace_layout(pl, n, 1, work, &ws);
+  int best = C0;
+  float best_ms = 0.f;
+  for (size_t i = 0; ok && i < cands.size(); ++i) {
+    set_slice_cluster(pl, cands[i]);
+    float t[3];
+    for (int run = 0; ok && run < 4; ++run) {
+      ok = cudaEventRecord(e0, 0) == cudaSuccess && launch_slice_forward(pl, x, n, 1, ws, 0) == cudaSuccess &&
+           launch_slice_inverse(pl, n, 1, kSynthInverse, ws, y, 0) == cudaSuccess &&
+           launch_slice_ola(pl, n, 1, ws, y, 0) == cudaSuccess && cudaEventRecord(e1, 0) == cudaSuccess &&
+           cudaEventSynchronize(e1) == cudaSuccess;
+      if (ok && run > 0) ok = cudaEventElapsedTime(&t[run - 1], e0, e1) == cudaSuccess;
+    }
+    if (!ok) break;
+    std::sort(t, t + 3);
+    if (i == 0 || t[1] < best_ms) {
+      best_ms = t[1];
+      best = cands[i];
+    }
+  }
+  cudaFree(x);
+  cudaFree(y);
+  cudaFree(work);
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  set_slice_cluster(pl, ok ? best : C0);
+}
+
 }  // namespace
 
 slicq_status build_tables(slicq_plan* pl) {
@@ -780,6 +836,7 @@ slicq_status build_tables(slicq_plan* pl) {
   cudaFree(d_d);
   cudaFree(d_bad);
   if (st == SLICQ_OK) calibrate_lanes(pl);
+  if (st == SLICQ_OK) tune_slice_cluster(pl);
   return st;
 }
 

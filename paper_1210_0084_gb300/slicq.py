@@ -78,6 +78,8 @@ def load_library():
         "slicq_plan_destroy": (None, [VP]),
         "slicq_plan_info": (ctypes.c_int, [VP, ctypes.POINTER(I32), ctypes.POINTER(I64)]),
         "slicq_plan_check": (ctypes.c_int, [VP]),
+        "slicq_plan_tuning": (ctypes.c_int, [VP, ctypes.POINTER(I32), ctypes.POINTER(I32),
+                                             ctypes.POINTER(I32)]),
         "slicq_num_slices": (I64, [VP, I64]),
         "slicq_workspace_size": (ctypes.c_int, [VP, I64, I64, ctypes.POINTER(SZ)]),
         "slicq_forward": (ctypes.c_int, [VP, VP, I64, I64, VP, I64, VP, SZ, VP]),
@@ -192,6 +194,14 @@ class SliCQPlan:
     @property
     def handle(self) -> ctypes.c_void_p:
         return self._h
+
+    @property
+    def slice_cluster(self) -> int:
+        """CTAs per slice the plan's slice kernels run (measured choice when
+        the parameters leave it at 0)."""
+        c = ctypes.c_int32()
+        _check(self.lib.slicq_plan_tuning(self._h, ctypes.byref(c), None, None), "slicq_plan_tuning")
+        return c.value
 
     def check(self):
         """Synchronise and raise SliCQError if a launch of this plan reported a

@@ -340,3 +340,44 @@ def test_multires_logmag_loss_backward(S):
     err = float(np.linalg.norm(g - gref))
     assert err <= REL * np.sqrt(scale2), (err, np.sqrt(scale2))
     assert abs(lgpu - lref) <= 1e-4 * lref, (lgpu, lref)
+
+
+@pytest.mark.parametrize("case", [
+    (16000.0, 50.0, 8000.0, 24, 2048, 512, 7000, 2, 1), (16000.0, 50.0, 8000.0, 24, 2048, 512, 7000, 2, 2),
+    (16000.0, 50.0, 8000.0, 24, 2048, 512, 7000, 2, 4), (16000.0, 50.0, 8000.0, 24, 2048, 512, 7000, 2, 8),
+    (48000.0, 50.0, 22000.0, 12, 16384, 4096, 30001, 2, 1), (48000.0, 50.0, 22000.0, 12, 16384, 4096, 30001, 2, 2),
+    (48000.0, 50.0, 22000.0, 12, 16384, 4096, 30001, 2, 4), (48000.0, 50.0, 22000.0, 12, 16384, 4096, 30001, 2, 8),
+    (44100.0, 32.7, 22050.0, 48, 65536, 16384, 150000, 1, 4), (44100.0, 32.7, 22050.0, 48, 65536, 16384, 150000, 1, 8),
+], ids=lambda c: f"L{c[4]}_C{c[8]}")
+def test_slice_cluster_sizes(S, case):
+    """Every slice cluster size a plan may run (given, or picked by the
+    plan's measurement): forward against the oracle, reconstruction, adjoint
+    of random coefficients."""
+    fs, fmin, fmax, B, L2, M, n, batch, C = case
+    p = S.SliCQParams(fs, fmin, fmax, B, L2, M, slice_cluster=C)
+    plan = S.SliCQPlan(p)
+    op = _oplan(p)
+    x = _signal(n, fs, batch, 700)
+    xd = torch.from_numpy(x).cuda()
+    c = plan.forward(xd)
+    y = plan.inverse(c, n)
+    cg = c.cpu().numpy().astype(np.complex128)
+    rng = np.random.default_rng(3)
+    cr = (rng.standard_normal(cg.shape) + 1j * rng.standard_normal(cg.shape)).astype(np.complex64)
+    ya = plan.adjoint(torch.from_numpy(cr).cuda(), n).cpu().numpy()
+    for b in range(batch):
+        _check_coefs(cg[b], O.slicq_forward(x[b].astype(np.float64), op))
+        assert _rel(y[b].cpu().numpy(), x[b]) <= REL
+        assert _rel(ya[b], O.slicq_adjoint(cr[b].astype(np.complex128), op, n)) <= REL
+
+
+def test_slice_cluster_tuned_choice_is_valid(S):
+    """With slice_cluster = 0 the plan measures the valid cluster sizes and
+    keeps one of them; the transform it runs is the same transform."""
+    p = S.SliCQParams(48000.0, 50.0, 22000.0, 12, 16384, 4096)
+    plan = S.SliCQPlan(p)
+    assert plan.slice_cluster in (1, 2, 4, 8)
+    op = _oplan(p)
+    x = _signal(30001, p.fs, 1, 77)
+    c = plan.forward(torch.from_numpy(x).cuda())
+    _check_coefs(c[0].cpu().numpy().astype(np.complex128), O.slicq_forward(x[0].astype(np.float64), op))
