@@ -218,8 +218,10 @@ class SliCQPlan:
         return sz.value
 
     def workspace(self, n: int, batch: int):
-        """Device workspace for (n, batch), cached on the plan."""
-        key = (int(n), int(batch))
+        """Device workspace for (n, batch) on the current stream, cached on the
+        plan: calls on different streams get different workspaces, so they may
+        run concurrently."""
+        key = (int(n), int(batch), self._torch.cuda.current_stream(self.device).cuda_stream)
         w = self._work.get(key)
         if w is None:
             nb = self.workspace_bytes(n, batch)
