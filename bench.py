@@ -235,13 +235,15 @@ def run_reference(args, x, rank, world):
     print(json.dumps(line), flush=True)
 
 
-def _config(world, mk_policy="pow2"):
+def _config(world, mk_policy="pow2", precision="fp32", slice_cluster=None):
     name = WORKLOAD_NAME + ("" if mk_policy == "pow2" else "; rectangular representation (one M_k)")
+    name += "" if precision == "fp32" else f"; band DFT stages {precision} on the tensor cores"
     return {"workload": name, "fs": WORKLOAD["fs"], "bins_per_octave": WORKLOAD["bins_per_octave"],
             "fmin": WORKLOAD["fmin"], "fmax": WORKLOAD["fmax"], "slice_len": WORKLOAD["slice_len"],
             "trans_len": WORKLOAD["trans_len"], "channels": WORKLOAD["channels"],
             "samples_per_channel": WORKLOAD["seconds"] * int(WORKLOAD["fs"]),
-            "mk_policy": mk_policy, "l2": "flushed between timed steps (256 MiB write, outside the events)",
+            "mk_policy": mk_policy, "precision": precision, "slice_cluster": slice_cluster,
+            "l2": "flushed between timed steps (256 MiB write, outside the events)",
             "parallelism": f"replicas x{world} (independent clips, no exchange)"}
 
 
@@ -400,6 +402,11 @@ def main():
                     help="skip the 1 s load phases around the timed region (for profiler runs)")
     ap.add_argument("--mk-policy", choices=("pow2", "const"), default="pow2",
                     help="band lengths: pow2 (headline) or const (rectangular representation)")
+    ap.add_argument("--precision", choices=("fp32", "split_fp16", "split_bf16"), default="fp32",
+                    help="band-DFT arithmetic of the timed step (fp32 is the headline)")
+    ap.add_argument("--slice-cluster", type=int, default=0,
+                    help="CTAs per slice FFT; 0 lets the plan time the valid sizes and keep the "
+                         "fastest (pin it under a profiler, whose serialised launches skew that timing)")
     ap.add_argument("--only-step", action="store_true",
                     help="time the step and its kernels only (no e2e, epilogue, streaming, "
                          "differentiation, precision or CPU measurements)")
@@ -440,7 +447,8 @@ def main():
     from paper_1210_0084_gb300.slicq import SliCQParams, SliCQPlan
 
     p = SliCQParams(WORKLOAD["fs"], WORKLOAD["fmin"], WORKLOAD["fmax"], WORKLOAD["bins_per_octave"],
-                    WORKLOAD["slice_len"], WORKLOAD["trans_len"], mk_policy=args.mk_policy)
+                    WORKLOAD["slice_len"], WORKLOAD["trans_len"], mk_policy=args.mk_policy,
+                    precision=args.precision, slice_cluster=args.slice_cluster)
     plan = SliCQPlan(p, local_rank)
     dev = torch.device("cuda", local_rank)
     stream = torch.cuda.current_stream(dev)
@@ -554,7 +562,7 @@ def main():
                 "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": _config(world, args.mk_policy), "recon_rel_err": recon_err,
+                "config": _config(world, args.mk_policy, args.precision, plan.slice_cluster), "recon_rel_err": recon_err,
                 "roofline": roofline, "step_roofline": step_roof, "kernels": kern,
                 "gpu_launches": len(traced), "clocks": sampler.summary(),
                 "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms)}), flush=True)
@@ -681,7 +689,7 @@ def main():
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": _config(world, args.mk_policy), "recon_rel_err": recon_err,
+            "config": _config(world, args.mk_policy, args.precision, plan.slice_cluster), "recon_rel_err": recon_err,
             "roofline": roofline, "step_roofline": step_roof, "kernels": kern, "epilogues": epilogues,
             "streaming": streaming, "differentiation": diff, "precision": prec_cmp,
             "gpu_launches": len(traced), "e2e": e2e, "cpu_baseline": cpu,
