@@ -51,6 +51,11 @@ R14 Transposition (Sec. 6) translates baseband coefficients along the
     channels; ours keep the channel's absolute frequency (R1 folds by the
     absolute bin), so a shift by s channels also modulates by the centre-bin
     difference (slicq_modify).
+R15 Proposition 4 relates the slice windows to full-length ones by
+    sampling, g_k[j] = g^L_k[j L/2N]; its proof periodises inverse DFTs,
+    which holds for the 1/n-normalised inverse DFT.  With the unitary DFT
+    (R1) the full-length system the sliCQ approximates has the continuous
+    windows times sqrt(2N/L) (full_length_system).
 
 Parity status: every public function is pinned by a test under ``tests/``
 (brute-force atoms, explicit frame operator, perfect reconstruction, tight
@@ -75,6 +80,7 @@ __all__ = [
     "slicq_inverse", "slicq_adjoint", "slicq_forward_complex",
     "slicq_inverse_complex", "atoms", "frame_operator_matrix",
     "num_slices", "padded_length", "two_layer_view", "slicq_spectrogram", "slicq_modify",
+    "full_length_system", "cqnsgt_forward", "two_layer_sum", "prop4_bound", "approximation_snr_db",
 ]
 
 # ---------------------------------------------------------------------------
@@ -644,3 +650,102 @@ def slicq_modify(coef: np.ndarray, plan: SliCQPlan, shift: int = 0,
     if mask is not None:
         c = c * mask
     return c
+
+
+# ---------------------------------------------------------------------------
+# Full-length CQ-NSGT and the sliCQ approximation (Sec. 4.2, Proposition 4)
+# ---------------------------------------------------------------------------
+
+
+def full_length_system(plan: SliCQPlan, L: int) -> NSGSystem:
+    """The CQ-NSGT system G(g^L, a) on C^L that the slice windows sample
+    (Proposition 4): the same continuous windows as the slice system (Table 1
+    centres, bandwidths of cq_table) sampled on L bins, and the same time
+    steps a_k = 2N / M_k, i.e. L / a_k = (L / 2N) M_k coefficients per
+    channel.  L is a multiple of 2N.
+
+    Reading R15: the proof of Proposition 4 uses that the inverse DFT of the
+    sampled window is the periodisation of the inverse DFT of the full one,
+    which holds for the 1/n-normalised inverse DFT.  With the unitary DFT of
+    Sec. 2.1 (reading R1) it holds when g_k[j] = sqrt(L/2N) g^L_k[j L/2N], so
+    the full-length windows here are the continuous windows times
+    sqrt(2N/L).  (When M_k = |J_k| the L-length band may be shorter than its
+    support; c_{n,k} = <f, T_{n a_k} g^L_k-check> is still what Algorithm 1
+    computes, by periodisation.)"""
+    L2 = plan.params.slice_len
+    if L % L2:
+        raise ValueError("L must be a multiple of the slice length 2N")
+    r = L // L2
+    sysL = nsg_system(plan.params, L)
+    scale = 1.0 / math.sqrt(r)
+    chans = [Channel(cl.j0, cl.g * scale, r * cs.M) for cl, cs in zip(sysL.channels, plan.sys.channels)]
+    return NSGSystem(L, sysL.K, chans, sysL.xi, sysL.Omega)
+
+
+def cqnsgt_forward(f: np.ndarray, plan: SliCQPlan) -> List[np.ndarray]:
+    """Full-length CQ-NSGT coefficients c_{n,k} of f in C^L (Algorithm 1 on
+    full_length_system), all 2K+2 channels, L = len(f)."""
+    f = np.asarray(f, dtype=np.complex128)
+    return nsgt_analysis(f, full_length_system(plan, f.shape[-1]))
+
+
+def two_layer_sum(coefs: Sequence[Sequence[np.ndarray]], plan: SliCQPlan) -> List[np.ndarray]:
+    """s^0 + s^1 for every channel from the slices' coefficients (the lists of
+    slicq_forward_complex): slice m's c^m_{n^s,k} is added at
+    n = n^s + (m-1) M_k / 2 (mod S M_k / 2), so time index n = m M_k/2 + n^s
+    holds c^m_{n^s + M_k/2} + c^{m+1}_{n^s} (proof of Proposition 4)."""
+    S = len(coefs)
+    out = []
+    for k, ch in enumerate(plan.sys.channels):
+        M = ch.M
+        total = S * M // 2
+        acc = np.zeros(total, dtype=np.complex128)
+        for m in range(S):
+            idx = (np.arange(M) + (m - 1) * M // 2) % total
+            np.add.at(acc, idx, coefs[m][k])
+        out.append(acc)
+    return out
+
+
+def prop4_bound(plan: SliCQPlan, L: int) -> List[np.ndarray]:
+    """Right-hand side of Proposition 4 divided by ||f||_2, per channel k and
+    n^s < N/a_k = M_k/2:
+        ||(1 - h_0 - h_1) T_{n^s a_k} g^L_k-check||
+      + ||(h_0 + h_1) sum_{j=1}^{L/2N-1} T_{n^s a_k + 2jN} g^L_k-check||,
+    with g^L_k-check = F^{-1} g^L_k and h_0, h_1 the slicing windows of slices
+    0 and 1 on C^L (slice m covers t = (m-1)N + j, j < 2N).  The bound holds
+    for every slice m (the proof's translation argument): entry n^s bounds
+    |s^0 + s^1 - c| at every n = m M_k/2 + n^s."""
+    N = plan.N
+    L2 = 2 * N
+    r = L // L2
+    sysL = full_length_system(plan, L)
+    j = np.arange(L2)
+    h01 = np.zeros(L)
+    np.add.at(h01, (j - N) % L, plan.h0)   # slice 0
+    np.add.at(h01, j % L, plan.h0)         # slice 1
+    out = []
+    l = np.arange(L)
+    for k, ch in enumerate(sysL.channels):
+        gk = unitary_idft(ch.full(L))
+        Mk = plan.sys.channels[k].M
+        a = L2 // Mk
+        ns = np.arange(Mk // 2)
+        A = gk[(l[None, :] - ns[:, None] * a) % L]                    # rows T_{n^s a} g-check
+        per = A.reshape(ns.size, r, L2).sum(axis=1)                    # sum over the 2N translates
+        over = np.tile(per, (1, r)) - A                                # j = 1 .. L/2N - 1
+        inner = np.linalg.norm((1.0 - h01)[None, :] * A, axis=1)
+        outer = np.linalg.norm(h01[None, :] * over, axis=1)
+        out.append(inner + outer)
+    return out
+
+
+def approximation_snr_db(f: np.ndarray, plan: SliCQPlan) -> float:
+    """20 log10(||c|| / ||c - (s^0 + s^1)||) over all channels (Sec. 5.3):
+    how closely the sliCQ of f approximates its full-length CQ-NSGT."""
+    f = np.asarray(f, dtype=np.complex128)
+    c = cqnsgt_forward(f, plan)
+    s = two_layer_sum(slicq_forward_complex(f, plan), plan)
+    num = math.sqrt(sum(float(np.sum(np.abs(ck) ** 2)) for ck in c))
+    den = math.sqrt(sum(float(np.sum(np.abs(ck - sk) ** 2)) for ck, sk in zip(c, s)))
+    return 20.0 * math.log10(num / den)

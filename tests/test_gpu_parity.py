@@ -381,3 +381,33 @@ def test_slice_cluster_tuned_choice_is_valid(S):
     x = _signal(30001, p.fs, 1, 77)
     c = plan.forward(torch.from_numpy(x).cuda())
     _check_coefs(c[0].cpu().numpy().astype(np.complex128), O.slicq_forward(x[0].astype(np.float64), op))
+
+
+@pytest.mark.parametrize("L2,M", [(2048, 512), (4096, 1024)])
+def test_slicq_spectrogram_approximates_full_length_cq(S, L2, M):
+    """Proposition 4 on the library's output: the sliCQ spectrogram
+    |s^0 + s^1|^2 of a real signal (GPU coefficients, GPU spectrogram kernel)
+    against the full-length CQ-NSGT |c| of the same signal (oracle, FP64, with
+    the windows of reading R15): ||s^0 + s^1| - |c|| <= ||f|| (inner + outer)
+    at every kept (n, k), plus float32 rounding (2e-5 of the largest value)."""
+    fs = 44100.0
+    p = S.SliCQParams(fs, 100.0, fs / 2, 12, L2, M)
+    plan = S.SliCQPlan(p)
+    op = _oplan(p)
+    n = 4 * L2
+    t = np.arange(n) / fs
+    x = (np.sin(2 * np.pi * 440.0 * t) + 0.5 * np.sin(2 * np.pi * 3100.0 * t)
+         + 0.05 * np.random.default_rng(8).standard_normal(n)).astype(np.float32)
+    xd = torch.from_numpy(x).cuda()
+    spec = plan.spectrogram(plan.forward(xd), n)
+    blocks = [np.sqrt(b.cpu().numpy().astype(np.float64)) for b in plan.spectrogram_blocks(spec, n)]
+    x64 = x.astype(np.float64)
+    c = O.cqnsgt_forward(x64, op)
+    bound = O.prop4_bound(op, n)
+    nf = float(np.linalg.norm(x64))
+    top = max(float(np.abs(ck).max()) for ck in c[: op.real_channels])
+    for k in range(op.real_channels):
+        reps = c[k].shape[0] // bound[k].shape[0]
+        assert blocks[k].shape == c[k].shape
+        gap = np.abs(blocks[k] - np.abs(c[k]))
+        assert np.all(gap <= nf * np.tile(bound[k], reps) + 2e-5 * top), k
