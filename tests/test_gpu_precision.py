@@ -106,3 +106,70 @@ def test_precision_rejects_unknown(S):
     cp.precision = 7
     h = ctypes.c_void_p()
     assert lib.slicq_plan_create(ctypes.byref(cp), 0, ctypes.byref(h)) == 1  # SLICQ_EINVAL
+
+
+def _sig(n, fs, seed):
+    return signals.noise_plus_sines(n, fs, seed)
+
+
+def test_split_ragged_batch(S):
+    """A ragged batch of split-FP16 plans: each clip's coefficients equal the
+    single-clip path of its plan bit for bit, and reconstruct to the FP32 bar."""
+    rates = [(16000.0, 24), (44100.0, 48), (48000.0, 96)]
+    plans = [S.SliCQPlan(S.SliCQParams(fs, 50.0, min(22000.0, fs / 2), B, 4096, 1024,
+                                       precision="split_fp16")) for fs, B in rates]
+    rng = np.random.default_rng(4)
+    clip_plan = [0, 1, 2, 1, 0, 2]
+    lens = [int(rng.uniform(0.1, 1.0) * rates[p][0]) for p in clip_plan]
+    xs = [_sig(n, rates[p][0], 40 + c) for c, (n, p) in enumerate(zip(lens, clip_plan))]
+    batch = S.SliCQBatch(plans, clip_plan, lens)
+    coef = batch.forward(batch.pack(xs))
+    rec = batch.inverse(coef)
+    torch.cuda.synchronize()
+    for c, x in enumerate(xs):
+        single = plans[clip_plan[c]].forward(torch.from_numpy(x).cuda()).cpu().numpy()
+        assert np.array_equal(batch.clip_coefs(coef, c).cpu().numpy(), single), c
+        assert _rel(batch.clip_signal(rec, c).cpu().numpy(), x) <= 1e-5, c
+    for p in plans:
+        p.check()
+
+
+def test_split_stream_matches_forward(S):
+    """Streaming one slice per call with a split-FP16 plan equals the plan's
+    forward slice by slice (signal ending in N zeros, as the streaming
+    tests require)."""
+    fs, L2, M = 16000.0, 4096, 1024
+    plan = S.SliCQPlan(S.SliCQParams(fs, 50.0, 8000.0, 24, L2, M, precision="split_fp16"))
+    N = L2 // 2
+    nblocks = 8
+    x = _sig(nblocks * N, fs, 55)
+    x[-N:] = 0.0
+    xd = torch.from_numpy(x).cuda()
+    c = plan.forward(xd)
+    st = S.SliCQStream(plan)
+    cs = torch.stack([st.forward(xd[m * N:(m + 1) * N]).clone() for m in range(nblocks)])
+    torch.cuda.synchronize()
+    assert torch.equal(cs, c)
+    plan.check()
+
+
+def test_split_masked_synthesis_and_backward(S):
+    """Masked synthesis (Sec. 6) and the autograd backward with split-FP16
+    band stages against the oracle, at the FP32 bars."""
+    fs, n = 44100.0, 30000
+    p = S.SliCQParams(fs, 50.0, 22050.0, 12, 8192, 2048, precision="split_fp16")
+    plan = S.SliCQPlan(p)
+    op = _oplan(p)
+    x = _sig(n, fs, 66)
+    xd = torch.from_numpy(x).cuda().requires_grad_(True)
+    c = S.slicq_transform(xd, plan)
+    mask = torch.from_numpy(np.random.default_rng(2).uniform(0.0, 2.0, size=c.shape).astype(np.float32)).cuda()
+    y = plan.inverse_modified(c.detach(), n, mask=mask).cpu().numpy()
+    cg = c.detach().cpu().numpy().astype(np.complex128)
+    ref = O.slicq_inverse(O.slicq_modify(cg, op, mask=mask.cpu().numpy().astype(np.float64)), op, n)
+    assert _rel(y, ref) <= 1e-5
+    (c.abs() ** 2).sum().backward()
+    g = xd.grad.cpu().numpy()
+    gref = 2.0 * O.slicq_adjoint(O.slicq_forward(x.astype(np.float64), op), op, n)
+    assert _rel(g, gref) <= 1e-5
+    plan.check()
