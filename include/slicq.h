@@ -181,6 +181,17 @@ SLICQ_API slicq_status slicq_plan_check(const slicq_plan* plan);
 SLICQ_API slicq_status slicq_plan_tuning(const slicq_plan* plan, int32_t* slice_cluster,
                                          int32_t* band_ctas_analysis, int32_t* band_ctas_synthesis);
 
+/*
+ * Self-test of the bounded device waits (the paper has no counterpart).
+ * One CTA on `device` waits, with the wait the split-precision band kernels
+ * use for their tensor-core products, on an mbarrier that nothing
+ * completes; after limit_cycles SM clocks it gives up.  Returns
+ * SLICQ_ETIMEOUT when the wait gave up (the expected result), SLICQ_OK if it
+ * completed, SLICQ_EINVAL for limit_cycles < 1, SLICQ_ECUDA on a CUDA
+ * error.  Synchronous; allocates one int; the context stays usable.
+ */
+SLICQ_API slicq_status slicq_selftest_wait(int device, int64_t limit_cycles);
+
 /* K + 2 and sum_k M_k of a plan. */
 SLICQ_API slicq_status slicq_plan_info(const slicq_plan* plan, int32_t* n_channels,
                              int64_t* coefs_per_slice);

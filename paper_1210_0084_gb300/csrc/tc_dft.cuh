@@ -93,8 +93,8 @@ __device__ __forceinline__ void tc_fence_after() {
 }
 
 // true once the mbarrier at `addr` has completed the phase with `parity`,
-// false after kTcWaitCycles
-__device__ __forceinline__ bool tc_wait(uint32_t addr, uint32_t parity) {
+// false after `limit` SM clocks
+__device__ __forceinline__ bool tc_wait(uint32_t addr, uint32_t parity, long long limit = kTcWaitCycles) {
   const long long t0 = clock64();
   for (;;) {
     uint32_t done;
@@ -105,7 +105,7 @@ __device__ __forceinline__ bool tc_wait(uint32_t addr, uint32_t parity) {
         : "r"(addr), "r"(parity)
         : "memory");
     if (done) return true;
-    if (clock64() - t0 > kTcWaitCycles) return false;
+    if (clock64() - t0 > limit) return false;
   }
 }
 

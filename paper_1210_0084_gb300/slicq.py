@@ -78,6 +78,7 @@ def load_library():
         "slicq_plan_destroy": (None, [VP]),
         "slicq_plan_info": (ctypes.c_int, [VP, ctypes.POINTER(I32), ctypes.POINTER(I64)]),
         "slicq_plan_check": (ctypes.c_int, [VP]),
+        "slicq_selftest_wait": (ctypes.c_int, [ctypes.c_int, I64]),
         "slicq_plan_tuning": (ctypes.c_int, [VP, ctypes.POINTER(I32), ctypes.POINTER(I32),
                                              ctypes.POINTER(I32)]),
         "slicq_num_slices": (I64, [VP, I64]),

@@ -173,3 +173,19 @@ def test_split_masked_synthesis_and_backward(S):
     gref = 2.0 * O.slicq_adjoint(O.slicq_forward(x.astype(np.float64), op), op, n)
     assert _rel(g, gref) <= 1e-5
     plan.check()
+
+
+def test_bounded_wait_gives_up_and_context_survives(S):
+    """The bounded wait of the tensor-core stages, on an mbarrier nothing
+    completes, gives up after its limit (about 0.5 ms here) and reports
+    SLICQ_ETIMEOUT; afterwards the device still runs a transform correctly."""
+    lib = S.load_library()
+    assert lib.slicq_selftest_wait(0, 1_000_000) == 5  # SLICQ_ETIMEOUT
+    assert lib.slicq_selftest_wait(0, 0) == 1          # SLICQ_EINVAL
+    p = S.SliCQParams(44100.0, 50.0, 22050.0, 12, 4096, 1024, precision="split_fp16")
+    plan = S.SliCQPlan(p)
+    x = signals.noise_plus_sines(20000, 44100.0, 91)
+    c = plan.forward(torch.from_numpy(x).cuda())
+    plan.check()
+    ref = O.slicq_forward(x.astype(np.float64), _oplan(p))
+    assert _rel(c.cpu().numpy().astype(np.complex128), ref) <= 1e-5
