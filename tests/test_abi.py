@@ -90,6 +90,35 @@ def test_invalid_parameters_are_rejected(lib, kw, code):
     assert lib.slicq_layout(ctypes.byref(cp), ctypes.byref(n), ctypes.byref(c)) == code
 
 
+def test_precision_values(lib):
+    """slicq_params.precision: the three defined values build a layout (the
+    split-precision ones with the same channels), anything else is EINVAL."""
+    base = dict(fs=44100.0, fmin=50.0, fmax=22050.0, bins_per_octave=12, slice_len=8192,
+                trans_len=2048)
+    counts = []
+    for prec in ("fp32", "split_fp16", "split_bf16"):
+        cp = S.SliCQParams(**base, precision=prec).to_c()
+        n, c = ctypes.c_int32(), ctypes.c_int64()
+        assert lib.slicq_layout(ctypes.byref(cp), ctypes.byref(n), ctypes.byref(c)) == 0
+        counts.append((n.value, c.value))
+    assert counts[0] == counts[1] == counts[2]
+    for bad in (3, -1, 7):
+        cp = S.SliCQParams(**base).to_c()
+        cp.precision = bad
+        n, c = ctypes.c_int32(), ctypes.c_int64()
+        assert lib.slicq_layout(ctypes.byref(cp), ctypes.byref(n), ctypes.byref(c)) == 1
+
+
+def test_selftest_and_tuning_reject_bad_arguments(lib):
+    """Argument checks that need no device: a non-positive wait limit, a
+    null plan."""
+    lib.slicq_selftest_wait.restype = ctypes.c_int
+    lib.slicq_selftest_wait.argtypes = [ctypes.c_int, ctypes.c_int64]
+    assert lib.slicq_selftest_wait(0, 0) == 1
+    assert lib.slicq_plan_tuning(None, None, None, None) == 1
+    assert lib.slicq_plan_check(None) == 1
+
+
 def test_null_pointers(lib):
     assert lib.slicq_layout(None, None, None) == 1
     assert lib.slicq_plan_info(None, None, None) == 1
