@@ -350,12 +350,34 @@ class SliCQPlan:
                                           out.numel(), self._stream()), "slicq_spectrogram")
         return out[0] if squeeze else out
 
+    def two_layer(self, c, k: int):
+        """(s0, s1) of channel k as views of the coefficients (see ``two_layer``)."""
+        lay = layout(self.params)
+        return two_layer(c, int(lay["off"][k]), int(lay["M"][k]))
+
     def spectrogram_blocks(self, spec, n: int):
         """Per-channel views [.., S M_k / 2] of a spectrogram from ``spectrogram``."""
         lay = layout(self.params)
         S = self.num_slices(n)
         return [spec[..., S * int(o) // 2: S * (int(o) + int(m)) // 2]
                 for o, m in zip(lay["off"], lay["M"])]
+
+
+def two_layer(c, off_k: int, M_k: int):
+    """The 2-layer array s^l_{n,k} of Sec. 4.1 for one channel, as views of
+    the coefficients (no copy).
+
+    c is [batch, S, coefs_per_slice] (or [S, coefs_per_slice]); channel k
+    occupies columns off_k .. off_k + M_k - 1 of every slice.  Slice m's
+    coefficient n^s sits in layer l = m mod 2 at time index
+    ((m - 1) M_k / 2 + n^s) mod (S M_k / 2); slices of one parity tile the
+    time axis.  Returns (s0, s1), each [..., S/2, M_k] with s^l[q, n^s] =
+    slice l + 2q: s1 row q covers time indices q M_k .. q M_k + M_k - 1, s0
+    row q covers q M_k - M_k/2 .. q M_k + M_k/2 - 1 (row 0's first half wraps
+    to the end).  s0 + s1 at equal time indices is the sliCQ spectrogram's
+    argument."""
+    blk = c[..., off_k:off_k + M_k]
+    return blk[..., 0::2, :], blk[..., 1::2, :]
 
 
 def _autograd():

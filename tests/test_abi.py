@@ -127,3 +127,29 @@ def test_null_pointers(lib):
     assert lib.slicq_inverse(None, None, 1, 1, None, None, 0, None) == 1
     assert lib.slicq_adjoint(None, None, 1, 1, None, None, 0, None) == 1
     assert lib.slicq_spectrogram(None, None, 1, 1, None, 0, None) == 1
+
+
+def test_two_layer_views_match_oracle():
+    """two_layer: views of the coefficient tensor that place every slice's
+    coefficients where the oracle's 2-layer array (Sec. 4.1) has them."""
+    torch = pytest.importorskip("torch")
+    p = S.SliCQParams(16000.0, 50.0, 8000.0, 24, 2048, 512)
+    op = O.make_plan(O.SliCQParams(p.fs, p.fmin, p.fmax, p.bins_per_octave, p.slice_len, p.trans_len))
+    x = np.random.default_rng(3).standard_normal(7000)
+    c = O.slicq_forward(x, op)
+    ct = torch.from_numpy(c)
+    lay = S.layout(p)
+    for k in (0, 5, op.K, op.K + 1):
+        M = int(lay["M"][k])
+        s0, s1 = S.two_layer(ct, int(lay["off"][k]), M)
+        # views of the coefficients, not copies
+        assert s0.untyped_storage().data_ptr() == ct.untyped_storage().data_ptr()
+        assert s1.untyped_storage().data_ptr() == ct.untyped_storage().data_ptr()
+        ref = O.two_layer_view(c, op, k)            # [2, S M / 2]
+        total = ref.shape[1]
+        # layer 1 row q starts at time q M; layer 0 row q at q M - M/2
+        got1 = s1.reshape(-1).numpy()
+        got0 = np.roll(s0.reshape(-1).numpy(), -M // 2)
+        np.testing.assert_array_equal(got1, ref[1])
+        np.testing.assert_array_equal(got0, ref[0])
+        assert got1.shape[0] == total
