@@ -28,8 +28,11 @@
  *   - Calls that take a stream are asynchronous on that stream.  They return
  *     argument errors before launching anything and launch errors at once;
  *     faults inside a kernel surface at the next synchronising call.
- *   - No entry point allocates device memory except slicq_plan_create and
- *     slicq_batch_create.
+ *   - No entry point allocates device memory except slicq_plan_create,
+ *     slicq_batch_create and slicq_stream_create (the objects they create
+ *     own it until destroyed) and slicq_selftest_wait (one int, freed
+ *     before it returns).  A plan's creation also allocates and frees
+ *     scratch for its own calibration runs.
  *   - Nothing throws across the ABI; every call returns a slicq_status.
  */
 #ifndef SLICQ_H
