@@ -350,6 +350,11 @@ class SliCQPlan:
                                           out.numel(), self._stream()), "slicq_spectrogram")
         return out[0] if squeeze else out
 
+    def channels(self, c):
+        """Per-channel views [..., S, M_k] of packed coefficients (see ``channel_views``)."""
+        lay = layout(self.params)
+        return channel_views(c, lay["off"], lay["M"])
+
     def two_layer(self, c, k: int):
         """(s0, s1) of channel k as views of the coefficients (see ``two_layer``)."""
         lay = layout(self.params)
@@ -361,6 +366,14 @@ class SliCQPlan:
         S = self.num_slices(n)
         return [spec[..., S * int(o) // 2: S * (int(o) + int(m)) // 2]
                 for o, m in zip(lay["off"], lay["M"])]
+
+
+def channel_views(c, offsets, lengths):
+    """Per-channel views of packed coefficients (no copy): for c of shape
+    [..., S, coefs_per_slice] the list of c[..., off_k:off_k + M_k], i.e. the
+    coefficients c^m_{n,k} of channel k as [..., S, M_k] (Algorithm 3's
+    output as a list over k = 0..K+1)."""
+    return [c[..., int(o):int(o) + int(m)] for o, m in zip(offsets, lengths)]
 
 
 def two_layer(c, off_k: int, M_k: int):
@@ -378,6 +391,10 @@ def two_layer(c, off_k: int, M_k: int):
     argument."""
     blk = c[..., off_k:off_k + M_k]
     return blk[..., 0::2, :], blk[..., 1::2, :]
+
+
+# The transform object under the name the PyTorch layer of the design uses.
+SliCQ = SliCQPlan
 
 
 def _autograd():

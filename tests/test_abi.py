@@ -153,3 +153,24 @@ def test_two_layer_views_match_oracle():
         np.testing.assert_array_equal(got1, ref[1])
         np.testing.assert_array_equal(got0, ref[0])
         assert got1.shape[0] == total
+
+
+def test_channel_views_split_packed_coefficients():
+    """channel_views: views of channel k = 0..K+1 that equal the oracle's
+    per-channel coefficients of every slice."""
+    torch = pytest.importorskip("torch")
+    p = S.SliCQParams(16000.0, 50.0, 8000.0, 24, 2048, 512)
+    op = O.make_plan(O.SliCQParams(p.fs, p.fmin, p.fmax, p.bins_per_octave, p.slice_len, p.trans_len))
+    x = np.random.default_rng(4).standard_normal(5000)
+    c = O.slicq_forward(x, op)
+    ct = torch.from_numpy(c)
+    lay = S.layout(p)
+    views = S.channel_views(ct, lay["off"], lay["M"])
+    assert len(views) == op.K + 2
+    xs = O.slicq_slices(x, op)
+    for k, v in enumerate(views):
+        assert v.untyped_storage().data_ptr() == ct.untyped_storage().data_ptr()
+        for m in (0, xs.shape[0] - 1):
+            ref = O.nsgt_analysis(xs[m], op.sys, [k])[0]
+            np.testing.assert_allclose(v[m].numpy(), ref, rtol=0, atol=1e-12 * np.abs(ref).max() + 1e-300)
+    assert S.SliCQ is S.SliCQPlan
