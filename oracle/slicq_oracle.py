@@ -60,7 +60,9 @@ R15 Proposition 4 relates the slice windows to full-length ones by
 Parity status: every public function is pinned by a test under ``tests/``
 (brute-force atoms, explicit frame operator, perfect reconstruction, tight
 frame energy, adjoint identity, closed forms of Table 1, partition of unity,
-time and frequency localisation of the sliCQ spectrogram).
+time and frequency localisation of the sliCQ spectrogram, FP64 gradcheck of
+the adjoint under a log-magnitude loss, and Proposition 4's bound between the
+sliCQ and the full-length CQ-NSGT at every time-frequency index).
 """
 
 from __future__ import annotations
