@@ -17,8 +17,9 @@ of the method) on the host cores instead.
 
 Beside the step the line reports the sliCQ spectrogram epilogue, the
 streaming mode's per-call latency, the differentiation workload
-(multi-resolution log-magnitude loss and its backward through the adjoint)
-and the split-precision tensor-core band DFTs against the FP32 form.
+(multi-resolution log-magnitude loss and its backward through the adjoint),
+the split-precision tensor-core band DFTs against the FP32 form, and the
+ragged batch of 256 clips over 16 plans (one CUDA-graph replay per step).
 """
 
 from __future__ import annotations
@@ -687,6 +688,7 @@ def main():
 
     diff = differentiation(dev, stream, flush, peak)
     prec_cmp = precision_compare(dev, stream, flush, x)
+    ragged = ragged_measure(rank, local_rank, steps=5, warmup=3) if world == 1 else None
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -700,6 +702,7 @@ def main():
             "config": _config(world, args.mk_policy, args.precision, plan.slice_cluster), "recon_rel_err": recon_err,
             "roofline": roofline, "step_roofline": step_roof, "kernels": kern, "epilogues": epilogues,
             "streaming": streaming, "differentiation": diff, "precision": prec_cmp,
+            "ragged_batch": ragged,
             "gpu_launches": len(traced), "e2e": e2e, "cpu_baseline": cpu,
             "clocks": sampler.summary(), "step_ms_min": min(step_ms), "step_ms_median": statistics.median(step_ms),
         }
@@ -709,24 +712,19 @@ def main():
         dist.destroy_process_group()
 
 
-def run_ragged(args, rank, world, local_rank):
+RAGGED_WORKLOAD = ("ragged batch: 256 mono clips, 1-30 s, fs {16, 22.05, 44.1, 48} kHz, "
+                   "B {12, 24, 48, 96}, fmin 50 Hz, fmax min(22 kHz, fs/2), 2N 16384, "
+                   "M 4096; one CUDA-graph replay per step")
+
+
+def ragged_measure(rank, local_rank, steps, warmup, world=1):
     """256 mono clips, lengths U[1, 30] s, fs in {16, 22.05, 44.1, 48} kHz, B in
     {12, 24, 48, 96}; fmin 50 Hz, fmax min(22 kHz, fs/2), 2N = 16384, M = 4096.
     One step = batch forward + batch inverse, captured once in a CUDA graph
-    (plans as parallel branches) and replayed."""
-    import numpy as np
+    (plans as parallel branches) and replayed.  Returns the measurements
+    (time max over ranks when world > 1)."""
     import torch
-    import torch.distributed as dist
     from paper_1210_0084_gb300 import signals
-
-    torch.cuda.set_device(local_rank)
-    if world > 1:
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-    if local_rank == 0:
-        from paper_1210_0084_gb300 import build as B
-        B.build()
-    if world > 1:
-        dist.barrier()
     from paper_1210_0084_gb300.slicq import SliCQBatch, SliCQParams, SliCQPlan
 
     clips = signals.ragged_clips(256, seed=signals.seed_for(3, rank))
@@ -749,18 +747,19 @@ def run_ragged(args, rank, world, local_rank):
         with torch.cuda.graph(g, stream=cs):
             batch.forward(sig, coef)
             batch.inverse(coef, rec)
-    for _ in range(args.warmup):
+    for _ in range(warmup):
         g.replay()
     torch.cuda.synchronize()
     err = max(float(torch.linalg.norm(batch.clip_signal(rec, c) - batch.clip_signal(sig, c)) /
                     torch.linalg.norm(batch.clip_signal(sig, c))) for c in range(len(clips)))
     stream = torch.cuda.current_stream()
-    st = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    en = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    st = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    en = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
     if world > 1:
+        import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
-    for i in range(args.steps):
+    for i in range(steps):
         flush.fill_(i & 255)
         st[i].record(stream)
         g.replay()
@@ -772,21 +771,39 @@ def run_ragged(args, rank, world, local_rank):
     step_bytes = sum(8 * lens[c] + 16 * int(batch.slices[c]) * plans[clip_plan[c]].coefs_per_slice
                      for c in range(len(clips)))
     peak, peak_kind = _peaks()
-    if rank == 0:
-        print(json.dumps({
-            "metric": METRIC, "value": total * world / (ms_max / 1e3), "unit": UNIT,
-            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
-            "config": {"workload": "ragged batch: 256 mono clips, 1-30 s, fs {16, 22.05, 44.1, 48} kHz, "
-                                   "B {12, 24, 48, 96}, fmin 50 Hz, fmax min(22 kHz, fs/2), 2N 16384, "
-                                   "M 4096; one CUDA-graph replay per step",
-                       "clips": len(clips), "plans": len(plans), "samples": total,
-                       "l2": "flushed between timed steps (256 MiB write, outside the events)"},
+    return {"workload": RAGGED_WORKLOAD, "clips": len(clips), "plans": len(plans), "samples": total,
+            "ms_per_step": ms_max, "samples_per_s": total * world / (ms_max / 1e3),
             "max_clip_recon_rel_err": err,
             "step_roofline": {"alg_bytes": step_bytes, "achieved": step_bytes / (ms * 1e-3) / 1e9,
                               "peak": peak, "frac": step_bytes / (ms * 1e-3) / 1e9 / peak,
-                              "peak_kind": f"of {peak_kind}"},
+                              "peak_kind": f"of {peak_kind}"}}
+
+
+def run_ragged(args, rank, world, local_rank):
+    """The ragged batch as the bench's workload: its own JSON line."""
+    import torch
+    import torch.distributed as dist
+
+    torch.cuda.set_device(local_rank)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    if local_rank == 0:
+        from paper_1210_0084_gb300 import build as B
+        B.build()
+    if world > 1:
+        dist.barrier()
+    r = ragged_measure(rank, local_rank, args.steps, args.warmup, world)
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": r["samples_per_s"], "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": RAGGED_WORKLOAD, "clips": r["clips"], "plans": r["plans"],
+                       "samples": r["samples"],
+                       "l2": "flushed between timed steps (256 MiB write, outside the events)"},
+            "max_clip_recon_rel_err": r["max_clip_recon_rel_err"],
+            "step_roofline": r["step_roofline"],
         }), flush=True)
     if world > 1:
         dist.barrier()
