@@ -174,3 +174,18 @@ def test_channel_views_split_packed_coefficients():
             ref = O.nsgt_analysis(xs[m], op.sys, [k])[0]
             np.testing.assert_allclose(v[m].numpy(), ref, rtol=0, atol=1e-12 * np.abs(ref).max() + 1e-300)
     assert S.SliCQ is S.SliCQPlan
+
+
+def test_without_a_gpu_calls_fail_with_a_status(lib):
+    """No device: plan creation and the device self-test return SLICQ_ECUDA
+    (no crash, no fallback), and the Python plan raises."""
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    cp = S.SliCQParams(44100.0, 50.0, 22050.0, 12, 8192, 2048).to_c()
+    h = ctypes.c_void_p()
+    assert lib.slicq_plan_create(ctypes.byref(cp), 0, ctypes.byref(h)) == 3
+    assert not h.value
+    assert lib.slicq_selftest_wait(0, 1000) == 3
+    with pytest.raises(Exception):
+        S.SliCQPlan(S.SliCQParams(44100.0, 50.0, 22050.0, 12, 8192, 2048))
