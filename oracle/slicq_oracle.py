@@ -483,10 +483,15 @@ class SliCQPlan:
         return int(self.M.sum())
 
 
-def make_plan(p: SliCQParams) -> SliCQPlan:
-    """Analysis system, canonical dual and slicing windows for one parameter set."""
+def make_plan(p: SliCQParams, real_signal: bool = True) -> SliCQPlan:
+    """Analysis system, canonical dual and slicing windows for one parameter set.
+
+    With real_signal=False the plan serves the complex-input functions
+    (slicq_forward_complex / slicq_inverse_complex, all 2K+2 channels) and
+    accepts band lengths that do not divide 2N (the mult4 policy); the
+    real-signal functions need every M_k to divide 2N (reading R12)."""
     sys_ = nsg_system(p, p.slice_len)
-    if any(p.slice_len % ch.M for ch in sys_.channels):
+    if real_signal and any(p.slice_len % ch.M for ch in sys_.channels):
         # channel 2K+2-k equals conj(channel k) only when M_k divides 2N
         raise ValueError("real-signal sliCQ needs every M_k to divide 2N")
     dual = dual_system(sys_)

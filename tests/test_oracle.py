@@ -520,3 +520,43 @@ def test_mask_selects_channels():
     e = _channel_energy(O.slicq_forward(O.slicq_inverse(O.slicq_modify(c, plan, mask=mask), plan, n), plan), plan)
     assert e[160:190].min() > 1e3 * e[:100].max()
     assert e[160:190].min() > 1e3 * e[260:].max()
+
+
+# --- mixed-radix band lengths (M_k the smallest multiple of 4 >= |J_k|) ---
+
+MULT4 = O.SliCQParams(44100.0, 50.0, 22050.0, 12, 2048, 512, mk_policy="mult4")
+
+
+def test_mult4_real_signal_plans_are_refused():
+    """A band length that does not divide 2N breaks the conjugate symmetry
+    of a real signal's dropped channels (reading R12)."""
+    with pytest.raises(ValueError):
+        O.make_plan(MULT4)
+
+
+def test_mult4_complex_perfect_reconstruction_and_redundancy():
+    """Algorithm 4 inverts Algorithm 3 with M_k multiples of 4 (Props. 1-3
+    need only M_k >= |J_k|), with fewer coefficients than powers of two."""
+    plan = O.make_plan(MULT4, real_signal=False)
+    Ms = [ch.M for ch in plan.sys.channels]
+    assert all(m % 4 == 0 and m >= ch.length for m, ch in zip(Ms, plan.sys.channels))
+    assert any(2048 % m for m in Ms)
+    pow2 = O.make_plan(O.SliCQParams(44100.0, 50.0, 22050.0, 12, 2048, 512))
+    assert sum(Ms) < sum(ch.M for ch in pow2.sys.channels)
+    rng = _rng(31)
+    f = rng.standard_normal(8192) + 1j * rng.standard_normal(8192)
+    fr = O.slicq_inverse_complex(O.slicq_forward_complex(f, plan), plan, f.shape[0])
+    assert np.linalg.norm(fr - f) / np.linalg.norm(f) < 1e-12
+
+
+def test_mult4_coefficients_equal_inner_products_with_atoms():
+    """With a_k = 2N / M_k fractional, c_{n,k} is still <f, F^{-1}(M_{-n a_k} g_k)>."""
+    p = O.SliCQParams(8000.0, 200.0, 4000.0, 3, 128, 32, min_filter_len=4, mk_policy="mult4")
+    sys_ = O.nsg_system(p, 128)
+    assert any(128 % ch.M for ch in sys_.channels)
+    rng = _rng(32)
+    f = rng.standard_normal(128) + 1j * rng.standard_normal(128)
+    c = O.nsgt_analysis(f, sys_)
+    for k in range(sys_.n_channels):
+        A = O.atoms(sys_, k)
+        np.testing.assert_allclose(c[k], A.conj() @ f, rtol=0, atol=1e-12 * np.linalg.norm(f) * 16)
